@@ -1,0 +1,211 @@
+/*
+ * qtm.h -- C ABI of the GB300 (sm_103a) quantum-trajectory library.
+ *
+ * The library runs the Monte Carlo wave-function method of Sawerwain &
+ * Wisniewska, "QTM: computational package using MPI protocol for quantum
+ * trajectories method" (arXiv 1810.03047), Algorithm 1 of Sec. 2.2, over an
+ * ensemble of trajectories on one GPU and averages the observables over the
+ * ensemble (Sec. 3).  The problem statement follows the paper's mpi_main
+ * (Sec. 3): a Hamiltonian H, collapse operators C_n, expectation operators A_k,
+ * an initial state, a time interval with output points, a tolerance and a number
+ * of trajectories.
+ *
+ * Conventions
+ *   - hbar = 1.  Each trajectory integrates dpsi/dt = -i H_eff psi with
+ *     H_eff = H - (i/2) sum_n C_n^dag C_n (Sec. 2.2, Eq. eqn:effective:hamiltonian);
+ *     the library forms H_eff itself from H and the C_n.
+ *   - Complex numbers are pairs of doubles (re, im), interleaved.
+ *   - Matrices are square, n x n, either CSR (the storage of Sec. 3, uCSRMatrix)
+ *     or dense row-major.
+ *   - Output 0 is the initial state at t[0]; output j is the state at t[j].
+ *   - The value recorded for observable k at output j of one trajectory is
+ *     Re<psi|A_k|psi> / <psi|psi>; the ensemble mean is the plain average over
+ *     trajectories (Sec. 3 averages per node and again at the master; with equal
+ *     shares that equals the plain average).
+ *   - Random numbers: Philox4x64-10 (Salmon et al., SC'11), key (seed, 0),
+ *     counter (jump index k, global trajectory id, 0, 0); words 0 and 1 map to
+ *     r_k (the norm threshold of Algorithm 1 steps (A)/(D)) and c_k (the channel
+ *     draw of step (C)) by ((w >> 11) + 0.5) * 2^-53, both in (0, 1).  Results
+ *     therefore depend only on (seed, trajectory id), not on how trajectories are
+ *     split over launches or GPUs.
+ *
+ * Ownership and threading
+ *   - Every pointer passed to qtm_create is a HOST pointer; the library validates
+ *     and copies the data, so the caller may free its buffers when qtm_create
+ *     returns.  Output pointers of qtm_expect / qtm_sums / qtm_traj_expect /
+ *     qtm_jumps are HOST pointers owned by the caller.
+ *   - A context owns all device memory it allocates.  Device memory comes from the
+ *     allocator installed with qtm_set_allocator (the Python binding installs the
+ *     PyTorch caching allocator), else from cudaMallocAsync on the context stream.
+ *   - All device work of a context is issued on the CUDA stream given to
+ *     qtm_create (NULL = the legacy default stream).  qtm_run is asynchronous;
+ *     qtm_expect, qtm_sums, qtm_stats, qtm_traj_expect and qtm_jumps synchronise
+ *     that stream.  A context must not be used from two host threads at once.
+ *
+ * Errors
+ *   - No C++ exception crosses this ABI; every call returns a qtm_status.
+ *   - Argument errors are reported by the call that receives them (QTM_ERR_ARG)
+ *     and a message is available from qtm_last_error(ctx) (or qtm_last_error(NULL)
+ *     when no context exists yet).
+ *   - Per-trajectory failures inside qtm_run (step limit, step-size underflow,
+ *     non-finite state, a jump with no channel) do not stop the other
+ *     trajectories; they are counted, and the first failure's code is returned by
+ *     the next synchronising call.  Outputs of a failed trajectory after the
+ *     failure are NaN.  This mirrors ZVODE's negative ISTATE being turned into an
+ *     error level (Sec. 3, zvode_method_for_mc).
+ */
+#ifndef QTM_H
+#define QTM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QTM_OK = 0,
+    QTM_ERR_ARG = 1,          /* invalid argument (message in qtm_last_error) */
+    QTM_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+    QTM_ERR_NOMEM = 3,        /* host or device allocation failed */
+    QTM_ERR_MAXSTEPS = 4,     /* a trajectory exceeded max_steps attempted steps */
+    QTM_ERR_STEPSIZE = 5,     /* step size fell below 1e-14 max(1, |t|) */
+    QTM_ERR_NONFINITE = 6,    /* a non-finite error norm (NaN/Inf state) */
+    QTM_ERR_NO_CHANNEL = 7,   /* the norm fell to r but every ||C_n psi|| was 0 */
+    QTM_ERR_TIMEOUT = 8,      /* reserved: a bounded device wait gave up */
+    QTM_ERR_STATE = 9,        /* call out of order (e.g. qtm_expect before qtm_run) */
+    QTM_ERR_UNSUPPORTED = 10  /* the problem has no kernel in this build (e.g. dim too large) */
+} qtm_status;
+
+enum { QTM_FORMAT_DENSE = 0, QTM_FORMAT_CSR = 1 };
+
+/* Arithmetic of the trajectory integration. */
+enum {
+    QTM_PREC_C128 = 0   /* complex128 state, operators and stage products (FP64 throughout) */
+};
+
+/* qtm_problem.flags */
+enum {
+    QTM_FLAG_RECORD_JUMPS = 1  /* keep the first max_jumps_recorded jump times/channels per trajectory */
+};
+
+/* A square complex operator (host memory, copied by qtm_create).
+ *   CSR:   row_ptr[n + 1] (row_ptr[0] = 0, non-decreasing), col_ind[nnz] in [0, n),
+ *          values[2 * nnz]; nnz = row_ptr[n].
+ *   dense: values[2 * n * n] row-major; row_ptr, col_ind ignored, nnz ignored. */
+typedef struct {
+    int32_t n;
+    int32_t format;            /* QTM_FORMAT_CSR or QTM_FORMAT_DENSE */
+    const int32_t *row_ptr;
+    const int32_t *col_ind;
+    const double *values;      /* (re, im) interleaved */
+    int64_t nnz;
+} qtm_op;
+
+/* The problem statement (host memory, copied by qtm_create). */
+typedef struct {
+    int32_t dim;               /* Hilbert-space dimension N >= 1 */
+    qtm_op H;                  /* system Hamiltonian, Hermitian within 1e-12 (relative) */
+    int32_t n_c;               /* number of collapse operators, >= 0 */
+    const qtm_op *C;           /* n_c collapse operators, channel order = array order */
+    int32_t n_obs;             /* number of observables, >= 0 */
+    const qtm_op *A;           /* n_obs Hermitian observables */
+    const double *psi0;        /* 2 * dim; normalised by the library (must be non-zero, finite) */
+    int32_t n_t;               /* number of output times, >= 1 */
+    const double *t;           /* n_t strictly increasing times; t[0] is the start time */
+    double rtol, atol;         /* Dormand-Prince error control: rtol > 0, atol >= 0 */
+    int32_t precision;         /* QTM_PREC_* */
+    int64_t max_steps;         /* attempted steps per trajectory before QTM_ERR_MAXSTEPS (> 0) */
+    int32_t flags;             /* QTM_FLAG_* */
+    int32_t max_jumps_recorded;/* with QTM_FLAG_RECORD_JUMPS: jumps kept per trajectory (>= 1) */
+} qtm_problem;
+
+typedef struct {
+    int64_t trajectories;      /* trajectories of the last qtm_run */
+    int64_t accepted;          /* accepted Dormand-Prince steps (all trajectories) */
+    int64_t rejected;          /* rejected steps */
+    int64_t rhs_evals;         /* products M psi (one column each), rejected steps included */
+    int64_t jumps;             /* quantum jumps */
+    int64_t root_iters;        /* Newton/bisection iterations of the jump-time search */
+    int64_t failed;            /* trajectories that stopped with an error */
+    int32_t first_error;       /* qtm_status of the first failure, QTM_OK if none */
+    int32_t kernel_group;      /* lanes per trajectory chosen by the library */
+    int32_t kernel_rows;       /* state rows per lane chosen by the library */
+    int32_t grid;              /* CTAs of the trajectory kernel */
+    int32_t block;             /* threads per CTA of the trajectory kernel */
+    int32_t reserved;
+    double kernel_ms;          /* device time of the trajectory kernel (CUDA events on the context stream) */
+    double reduce_ms;          /* device time of the ensemble reduction */
+} qtm_stats_t;
+
+typedef struct qtm_ctx qtm_ctx;
+
+/* Device allocator hooks.  alloc returns device memory usable on `stream` or
+ * NULL; free releases it.  Installing NULL hooks restores cudaMallocAsync /
+ * cudaFreeAsync.  Contexts keep the hooks that were installed when they were
+ * created.  Not thread-safe with concurrent qtm_create calls. */
+typedef void *(*qtm_alloc_fn)(size_t bytes, void *stream, void *user);
+typedef void (*qtm_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
+qtm_status qtm_set_allocator(qtm_alloc_fn alloc, qtm_free_fn free_fn, void *user);
+
+/* Validates and copies the problem, forms H_eff, uploads the operators to the
+ * current CUDA device and returns a context bound to cuda_stream (a
+ * cudaStream_t, may be NULL).  On error *out is NULL and the message is
+ * available from qtm_last_error(NULL). */
+qtm_status qtm_create(const qtm_problem *problem, void *cuda_stream, qtm_ctx **out);
+
+/* Runs trajectories 0 .. ntraj-1 of the ensemble keyed by seed (asynchronous).
+ * ntraj >= 0.  Replaces the results of any previous run of this context. */
+qtm_status qtm_run(qtm_ctx *ctx, int64_t ntraj, uint64_t seed);
+
+/* Same for global trajectory ids first .. first+ntraj-1 (first >= 0): a shard of a
+ * larger ensemble, e.g. one GPU's share.  Results equal those of the same ids in
+ * a single larger run. */
+qtm_status qtm_run_range(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64_t seed);
+
+/* Ensemble mean (n_t * n_obs doubles, output-major: [j * n_obs + k]) and, if
+ * stderr_out is not NULL, the standard error sqrt(var / n) with the sample
+ * variance (n - 1 divisor; 0 when n < 2).  Synchronises; returns the first
+ * per-trajectory failure of the run, if any. */
+qtm_status qtm_expect(qtm_ctx *ctx, double *mean, double *stderr_out);
+
+/* Raw FP64 sums over the run's trajectories, for combining shards:
+ * sum[j * n_obs + k] = sum_i x_i, sumsq = sum_i x_i^2, *count = trajectories. */
+qtm_status qtm_sums(qtm_ctx *ctx, double *sum, double *sumsq, int64_t *count);
+
+/* Asynchronous device-side copy of the same sums into caller-owned DEVICE buffers
+ * (n_t * n_obs doubles each), ordered on the context stream; for combining shards
+ * with a collective (the averaging of Sec. 3 restated as one all-reduce) without
+ * a host round trip. */
+qtm_status qtm_sums_device(qtm_ctx *ctx, double *sum_dev, double *sumsq_dev);
+
+/* Per-trajectory values of the last run, [traj][j][k] (ntraj * n_t * n_obs doubles). */
+qtm_status qtm_traj_expect(qtm_ctx *ctx, double *out);
+
+/* Jump records of the last run (needs QTM_FLAG_RECORD_JUMPS): n_jumps[ntraj] total
+ * jumps per trajectory; jump_t / jump_ch [ntraj][max_jumps_recorded] hold the first
+ * max_jumps_recorded jump times and channel indices (unused slots: NaN / -1). */
+qtm_status qtm_jumps(qtm_ctx *ctx, int32_t *n_jumps, double *jump_t, int32_t *jump_ch);
+
+/* Counters of the last run (synchronises). */
+qtm_status qtm_stats(qtm_ctx *ctx, qtm_stats_t *out);
+
+/* Human-readable message of the last error of ctx (or of the last failed
+ * qtm_create when ctx is NULL).  Never NULL; valid until the next call. */
+const char *qtm_last_error(const qtm_ctx *ctx);
+
+/* Name of a status code, e.g. "QTM_ERR_ARG". */
+const char *qtm_status_string(qtm_status status);
+
+/* Releases the context's device memory (after synchronising its stream). NULL is ignored. */
+void qtm_destroy(qtm_ctx *ctx);
+
+/* Library version string, e.g. "0.1.0 sm_103a". */
+const char *qtm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QTM_H */

@@ -1,0 +1,119 @@
+// ensemble_reduce.cu -- the average over trajectories (Sec. 3: every node averages
+// its trajectories, the master averages again).  Here one GPU holds every
+// trajectory's values, [ntraj][P] with P = n_t * n_obs, and reduces them in FP64
+// in a fixed order: S contiguous segments of trajectories are summed
+// sequentially (threads run along P, so every load is coalesced), then the S
+// partial sums are added in segment order.  The standard error takes a second
+// pass over the deviations from the mean.  No floating-point atomics are used,
+// so the result is bitwise reproducible for a given trajectory count.
+#include "qtm_launch.h"
+
+namespace qtm {
+
+namespace {
+constexpr int kThreads = 128;
+constexpr long long kSegLen = 128;   // trajectories per segment
+constexpr int kMaxSegments = 4096;
+
+long long segment_length(long long ntraj)
+{
+    long long seg = kSegLen;
+    while ((ntraj + seg - 1) / seg > kMaxSegments) seg *= 2;
+    return seg;
+}
+
+// Pass 1: per segment, sum x and sum x^2 (the raw sums reported for combining shards).
+__global__ void __launch_bounds__(kThreads)
+segment_sums(const double *__restrict__ x, long long ntraj, int P, long long seg_len,
+             double *__restrict__ psum, double *__restrict__ psq)
+{
+    const int p = blockIdx.x * kThreads + threadIdx.x;
+    const long long s = blockIdx.y;
+    if (p >= P) return;
+    const long long b0 = s * seg_len;
+    const long long b1 = b0 + seg_len < ntraj ? b0 + seg_len : ntraj;
+    double sum = 0.0, sq = 0.0;
+    for (long long b = b0; b < b1; ++b) {
+        const double v = x[b * P + p];
+        sum += v;
+        sq = fma(v, v, sq);
+    }
+    psum[s * P + p] = sum;
+    psq[s * P + p] = sq;
+}
+
+// Segment partials added in segment order; the mean follows.
+__global__ void __launch_bounds__(kThreads)
+combine_sums(const double *__restrict__ psum, const double *__restrict__ psq, int S, int P,
+             long long ntraj, double *sum, double *sumsq, double *mean)
+{
+    const int p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= P) return;
+    double s1 = 0.0, s2 = 0.0;
+    for (int s = 0; s < S; ++s) {
+        s1 += psum[(long long)s * P + p];
+        s2 += psq[(long long)s * P + p];
+    }
+    sum[p] = s1;
+    sumsq[p] = s2;
+    mean[p] = ntraj > 0 ? s1 / (double)ntraj : 0.0;
+}
+
+// Pass 2: per segment, sum (x - mean)^2, so the variance does not suffer the
+// cancellation of sum x^2 - (sum x)^2 / n when the spread is small.
+__global__ void __launch_bounds__(kThreads)
+segment_devs(const double *__restrict__ x, long long ntraj, int P, long long seg_len,
+             const double *__restrict__ mean, double *__restrict__ pdev)
+{
+    const int p = blockIdx.x * kThreads + threadIdx.x;
+    const long long s = blockIdx.y;
+    if (p >= P) return;
+    const long long b0 = s * seg_len;
+    const long long b1 = b0 + seg_len < ntraj ? b0 + seg_len : ntraj;
+    const double m = mean[p];
+    double d2 = 0.0;
+    for (long long b = b0; b < b1; ++b) {
+        const double d = x[b * P + p] - m;
+        d2 = fma(d, d, d2);
+    }
+    pdev[s * P + p] = d2;
+}
+
+// Standard error sqrt(var / n) with the sample variance (n - 1 divisor).
+__global__ void __launch_bounds__(kThreads)
+combine_devs(const double *__restrict__ pdev, int S, int P, long long ntraj, double *se)
+{
+    const int p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= P) return;
+    double d2 = 0.0;
+    for (int s = 0; s < S; ++s) d2 += pdev[(long long)s * P + p];
+    const double nt = (double)ntraj;
+    se[p] = ntraj > 1 ? sqrt(d2 / (nt - 1.0) / nt) : 0.0;
+}
+}  // namespace
+
+int reduce_segments(long long ntraj)
+{
+    const long long seg = segment_length(ntraj);
+    const long long S = (ntraj + seg - 1) / seg;
+    return (int)(S < 1 ? 1 : S);
+}
+
+cudaError_t launch_ensemble_reduce(const double *out, long long ntraj, int P, double *partial,
+                                   double *sum, double *sumsq, double *mean, double *se,
+                                   cudaStream_t stream)
+{
+    if (P <= 0) return cudaSuccess;
+    const int S = reduce_segments(ntraj);
+    const long long seg = segment_length(ntraj);
+    double *psum = partial, *psq = partial + (size_t)S * P;
+    const dim3 grid_seg((P + kThreads - 1) / kThreads, S);
+    const unsigned grid_p = (P + kThreads - 1) / kThreads;
+    segment_sums<<<grid_seg, kThreads, 0, stream>>>(out, ntraj, P, seg, psum, psq);
+    combine_sums<<<grid_p, kThreads, 0, stream>>>(psum, psq, S, P, ntraj, sum, sumsq, mean);
+    segment_devs<<<grid_seg, kThreads, 0, stream>>>(out, ntraj, P, seg, mean, psum);
+    combine_devs<<<grid_p, kThreads, 0, stream>>>(psum, S, P, ntraj, se);
+    return cudaGetLastError();
+}
+
+}  // namespace qtm

@@ -1,0 +1,642 @@
+// qtm_api.cpp -- host side of the C ABI declared in include/qtm.h.
+//
+// qtm_create validates the problem statement (the inputs of the paper's
+// mpi_main, Sec. 3), forms M = -i H_eff = -i H - (1/2) sum_n C_n^dag C_n
+// (Sec. 2.2, Eq. eqn:effective:hamiltonian; hbar = 1, the stored form of the
+// Sec. 4.1 listing), normalises psi0, packs every operator into one CSR blob and
+// uploads it.  qtm_run launches the trajectory kernel and the ensemble
+// reduction on the context's stream; the synchronising calls copy results back.
+// No numerical step of a trajectory runs on the host.
+
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/qtm.h"
+#include "qtm_launch.h"
+
+using cd = std::complex<double>;
+using qtm::KernelArgs;
+using qtm::LaunchInfo;
+using qtm::OpOffsets;
+
+namespace {
+
+struct Allocator {
+    qtm_alloc_fn alloc = nullptr;
+    qtm_free_fn free = nullptr;
+    void *user = nullptr;
+};
+
+Allocator g_allocator;
+thread_local std::string g_create_error;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Csr {
+    int n = 0;
+    std::vector<int> rp, ci;
+    std::vector<cd> val;
+};
+
+}  // namespace
+
+struct qtm_ctx {
+    cudaStream_t stream = nullptr;
+    Allocator alloc;
+    int device = 0;
+    int n = 0, n_c = 0, n_obs = 0, n_t = 0;
+    int precision = 0, flags = 0, max_jumps = 0;
+    double rtol = 0, atol = 0;
+    long long max_steps = 0;
+    std::vector<int> ints;
+    std::vector<cd> vals;
+    std::vector<OpOffsets> ops;
+    std::vector<double> t;
+    std::vector<cd> psi0;
+    DevBuf d_ints, d_vals, d_t, d_psi0, d_queue, d_counters, d_first_error;
+    DevBuf d_out, d_partial, d_stats, d_njumps, d_jump_t, d_jump_ch;
+    long long last_ntraj = -1;
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // kernel start, kernel end, reduction end
+    bool timed = false;
+    LaunchInfo info{};
+    std::string err;
+};
+
+namespace {
+
+qtm_status fail(qtm_ctx *ctx, qtm_status st, const std::string &msg)
+{
+    if (ctx)
+        ctx->err = msg;
+    else
+        g_create_error = msg;
+    return st;
+}
+
+qtm_status cuda_fail(qtm_ctx *ctx, cudaError_t e, const char *what)
+{
+    std::string msg = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(ctx, QTM_ERR_CUDA, msg);
+}
+
+cudaError_t dev_alloc(qtm_ctx *ctx, DevBuf &b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    void *p = nullptr;
+    if (ctx->alloc.alloc) {
+        p = ctx->alloc.alloc(bytes, (void *)ctx->stream, ctx->alloc.user);
+        if (!p) return cudaErrorMemoryAllocation;
+    } else {
+        cudaError_t e = cudaMallocAsync(&p, bytes, ctx->stream);
+        if (e != cudaSuccess) return e;
+    }
+    b.p = p;
+    b.bytes = bytes;
+    return cudaSuccess;
+}
+
+void dev_free(qtm_ctx *ctx, DevBuf &b)
+{
+    if (!b.p) return;
+    if (ctx->alloc.free)
+        ctx->alloc.free(b.p, b.bytes, (void *)ctx->stream, ctx->alloc.user);
+    else
+        cudaFreeAsync(b.p, ctx->stream);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// grows b to at least `bytes` (contents are not preserved)
+cudaError_t dev_reserve(qtm_ctx *ctx, DevBuf &b, size_t bytes)
+{
+    if (b.p && b.bytes >= bytes) return cudaSuccess;
+    dev_free(ctx, b);
+    return dev_alloc(ctx, b, bytes);
+}
+
+bool is_finite(double x) { return std::isfinite(x); }
+
+// Copies a user operator into CSR form, checking its structure.
+qtm_status read_op(const qtm_op &op, int n, const char *name, Csr &out)
+{
+    char buf[256];
+    if (op.n != n) {
+        std::snprintf(buf, sizeof buf, "%s: n = %d differs from dim = %d", name, op.n, n);
+        return fail(nullptr, QTM_ERR_ARG, buf);
+    }
+    out.n = n;
+    out.rp.assign(n + 1, 0);
+    out.ci.clear();
+    out.val.clear();
+    if (op.format == QTM_FORMAT_DENSE) {
+        if (!op.values) return fail(nullptr, QTM_ERR_ARG, std::string(name) + ": dense values are NULL");
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < n; ++j) {
+                const double re = op.values[2 * ((size_t)i * n + j)];
+                const double im = op.values[2 * ((size_t)i * n + j) + 1];
+                if (!is_finite(re) || !is_finite(im))
+                    return fail(nullptr, QTM_ERR_ARG, std::string(name) + ": non-finite entry");
+                if (re != 0.0 || im != 0.0) {
+                    out.ci.push_back(j);
+                    out.val.emplace_back(re, im);
+                }
+            }
+            out.rp[i + 1] = (int)out.ci.size();
+        }
+        return QTM_OK;
+    }
+    if (op.format != QTM_FORMAT_CSR)
+        return fail(nullptr, QTM_ERR_ARG, std::string(name) + ": unknown format");
+    if (!op.row_ptr) return fail(nullptr, QTM_ERR_ARG, std::string(name) + ": row_ptr is NULL");
+    if (op.row_ptr[0] != 0) return fail(nullptr, QTM_ERR_ARG, std::string(name) + ": row_ptr[0] != 0");
+    for (int i = 0; i < n; ++i)
+        if (op.row_ptr[i + 1] < op.row_ptr[i])
+            return fail(nullptr, QTM_ERR_ARG, std::string(name) + ": row_ptr decreases");
+    const int64_t nnz = op.row_ptr[n];
+    if (nnz != op.nnz) {
+        std::snprintf(buf, sizeof buf, "%s: nnz = %lld but row_ptr[n] = %lld", name, (long long)op.nnz,
+                      (long long)nnz);
+        return fail(nullptr, QTM_ERR_ARG, buf);
+    }
+    if (nnz > 0 && (!op.col_ind || !op.values))
+        return fail(nullptr, QTM_ERR_ARG, std::string(name) + ": col_ind/values are NULL");
+    for (int i = 0; i < n; ++i) {
+        for (int k = op.row_ptr[i]; k < op.row_ptr[i + 1]; ++k) {
+            const int c = op.col_ind[k];
+            if (c < 0 || c >= n) {
+                std::snprintf(buf, sizeof buf, "%s: column index %d out of range in row %d", name, c, i);
+                return fail(nullptr, QTM_ERR_ARG, buf);
+            }
+            const double re = op.values[2 * (size_t)k], im = op.values[2 * (size_t)k + 1];
+            if (!is_finite(re) || !is_finite(im))
+                return fail(nullptr, QTM_ERR_ARG, std::string(name) + ": non-finite entry");
+            out.ci.push_back(c);
+            out.val.emplace_back(re, im);
+        }
+        out.rp[i + 1] = (int)out.ci.size();
+    }
+    return QTM_OK;
+}
+
+// Hermiticity within 1e-12 of the largest entry (duplicate entries are summed).
+bool is_hermitian(const Csr &a)
+{
+    std::vector<std::map<int, cd>> rows(a.n);
+    double amax = 0.0;
+    for (int i = 0; i < a.n; ++i)
+        for (int k = a.rp[i]; k < a.rp[i + 1]; ++k) {
+            rows[i][a.ci[k]] += a.val[k];
+            amax = std::max(amax, std::abs(a.val[k]));
+        }
+    const double tol = 1e-12 * std::max(1.0, amax);
+    for (int i = 0; i < a.n; ++i)
+        for (const auto &kv : rows[i]) {
+            auto it = rows[kv.first].find(i);
+            const cd other = it == rows[kv.first].end() ? cd(0.0) : it->second;
+            if (std::abs(kv.second - std::conj(other)) > tol) return false;
+        }
+    return true;
+}
+
+// M = -i H - (1/2) sum_n C_n^dag C_n; (C^dag C)_{ij} = sum_k conj(C_ki) C_kj.
+// Entries are accumulated in the order H, then channel by channel, row by row.
+Csr effective_matrix(const Csr &H, const std::vector<Csr> &C)
+{
+    const int n = H.n;
+    std::vector<std::map<int, cd>> rows(n);
+    for (int i = 0; i < n; ++i)
+        for (int k = H.rp[i]; k < H.rp[i + 1]; ++k) rows[i][H.ci[k]] += cd(0.0, -1.0) * H.val[k];
+    for (const Csr &c : C)
+        for (int k = 0; k < n; ++k)
+            for (int a = c.rp[k]; a < c.rp[k + 1]; ++a)
+                for (int b = c.rp[k]; b < c.rp[k + 1]; ++b)
+                    rows[c.ci[a]][c.ci[b]] += -0.5 * std::conj(c.val[a]) * c.val[b];
+    Csr M;
+    M.n = n;
+    M.rp.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        for (const auto &kv : rows[i])
+            if (kv.second != cd(0.0)) {
+                M.ci.push_back(kv.first);
+                M.val.push_back(kv.second);
+            }
+        M.rp[i + 1] = (int)M.ci.size();
+    }
+    return M;
+}
+
+void pack(qtm_ctx *ctx, const Csr &a)
+{
+    OpOffsets o;
+    o.rp = (int)ctx->ints.size();
+    ctx->ints.insert(ctx->ints.end(), a.rp.begin(), a.rp.end());
+    o.ci = (int)ctx->ints.size();
+    ctx->ints.insert(ctx->ints.end(), a.ci.begin(), a.ci.end());
+    o.val = (int)ctx->vals.size();
+    ctx->vals.insert(ctx->vals.end(), a.val.begin(), a.val.end());
+    ctx->ops.push_back(o);
+}
+
+void destroy_ctx(qtm_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    DevBuf *bufs[] = {&ctx->d_ints, &ctx->d_vals, &ctx->d_t, &ctx->d_psi0, &ctx->d_queue,
+                      &ctx->d_counters, &ctx->d_first_error, &ctx->d_out, &ctx->d_partial,
+                      &ctx->d_stats, &ctx->d_njumps, &ctx->d_jump_t, &ctx->d_jump_ch};
+    for (DevBuf *b : bufs) dev_free(ctx, *b);
+    cudaStreamSynchronize(ctx->stream);
+    for (cudaEvent_t &e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    delete ctx;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *qtm_version(void) { return "0.1.0 sm_103a"; }
+
+const char *qtm_status_string(qtm_status s)
+{
+    switch (s) {
+    case QTM_OK: return "QTM_OK";
+    case QTM_ERR_ARG: return "QTM_ERR_ARG";
+    case QTM_ERR_CUDA: return "QTM_ERR_CUDA";
+    case QTM_ERR_NOMEM: return "QTM_ERR_NOMEM";
+    case QTM_ERR_MAXSTEPS: return "QTM_ERR_MAXSTEPS";
+    case QTM_ERR_STEPSIZE: return "QTM_ERR_STEPSIZE";
+    case QTM_ERR_NONFINITE: return "QTM_ERR_NONFINITE";
+    case QTM_ERR_NO_CHANNEL: return "QTM_ERR_NO_CHANNEL";
+    case QTM_ERR_TIMEOUT: return "QTM_ERR_TIMEOUT";
+    case QTM_ERR_STATE: return "QTM_ERR_STATE";
+    case QTM_ERR_UNSUPPORTED: return "QTM_ERR_UNSUPPORTED";
+    }
+    return "QTM_ERR_UNKNOWN";
+}
+
+const char *qtm_last_error(const qtm_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+qtm_status qtm_set_allocator(qtm_alloc_fn alloc, qtm_free_fn free_fn, void *user)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(nullptr, QTM_ERR_ARG, "qtm_set_allocator: alloc and free must both be set or both NULL");
+    g_allocator.alloc = alloc;
+    g_allocator.free = free_fn;
+    g_allocator.user = user;
+    return QTM_OK;
+}
+
+qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
+{
+    g_create_error.clear();
+    if (!out) return fail(nullptr, QTM_ERR_ARG, "qtm_create: out is NULL");
+    *out = nullptr;
+    if (!p) return fail(nullptr, QTM_ERR_ARG, "qtm_create: problem is NULL");
+    const int n = p->dim;
+    char buf[256];
+    if (n < 1) return fail(nullptr, QTM_ERR_ARG, "qtm_create: dim must be >= 1");
+    if (p->n_c < 0 || p->n_obs < 0) return fail(nullptr, QTM_ERR_ARG, "qtm_create: negative operator count");
+    if (p->n_c > 0 && !p->C) return fail(nullptr, QTM_ERR_ARG, "qtm_create: C is NULL");
+    if (p->n_obs > 0 && !p->A) return fail(nullptr, QTM_ERR_ARG, "qtm_create: A is NULL");
+    if (p->n_t < 1 || !p->t) return fail(nullptr, QTM_ERR_ARG, "qtm_create: need n_t >= 1 output times");
+    for (int i = 0; i < p->n_t; ++i)
+        if (!is_finite(p->t[i])) return fail(nullptr, QTM_ERR_ARG, "qtm_create: non-finite output time");
+    for (int i = 1; i < p->n_t; ++i)
+        if (!(p->t[i] > p->t[i - 1]))
+            return fail(nullptr, QTM_ERR_ARG, "qtm_create: output times must be strictly increasing");
+    if (!(p->rtol > 0.0) || !(p->atol >= 0.0) || !is_finite(p->rtol) || !is_finite(p->atol))
+        return fail(nullptr, QTM_ERR_ARG, "qtm_create: need rtol > 0 and atol >= 0");
+    if (p->max_steps <= 0) return fail(nullptr, QTM_ERR_ARG, "qtm_create: max_steps must be > 0");
+    if (p->precision != QTM_PREC_C128)
+        return fail(nullptr, QTM_ERR_ARG, "qtm_create: unknown precision");
+    if ((p->flags & ~QTM_FLAG_RECORD_JUMPS) != 0) return fail(nullptr, QTM_ERR_ARG, "qtm_create: unknown flags");
+    if ((p->flags & QTM_FLAG_RECORD_JUMPS) && p->max_jumps_recorded < 1)
+        return fail(nullptr, QTM_ERR_ARG, "qtm_create: RECORD_JUMPS needs max_jumps_recorded >= 1");
+    if (!p->psi0) return fail(nullptr, QTM_ERR_ARG, "qtm_create: psi0 is NULL");
+
+    Csr H;
+    qtm_status st = read_op(p->H, n, "H", H);
+    if (st) return st;
+    if (!is_hermitian(H)) return fail(nullptr, QTM_ERR_ARG, "qtm_create: H is not Hermitian (tolerance 1e-12)");
+    std::vector<Csr> C(p->n_c), A(p->n_obs);
+    for (int i = 0; i < p->n_c; ++i) {
+        std::snprintf(buf, sizeof buf, "C[%d]", i);
+        if ((st = read_op(p->C[i], n, buf, C[i]))) return st;
+    }
+    for (int i = 0; i < p->n_obs; ++i) {
+        std::snprintf(buf, sizeof buf, "A[%d]", i);
+        if ((st = read_op(p->A[i], n, buf, A[i]))) return st;
+        if (!is_hermitian(A[i])) {
+            std::snprintf(buf, sizeof buf, "qtm_create: A[%d] is not Hermitian (tolerance 1e-12)", i);
+            return fail(nullptr, QTM_ERR_ARG, buf);
+        }
+    }
+    double nn = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double re = p->psi0[2 * i], im = p->psi0[2 * i + 1];
+        if (!is_finite(re) || !is_finite(im)) return fail(nullptr, QTM_ERR_ARG, "qtm_create: non-finite psi0");
+        nn += re * re + im * im;
+    }
+    if (!(nn > 0.0)) return fail(nullptr, QTM_ERR_ARG, "qtm_create: psi0 is zero");
+    if (1 + p->n_c + p->n_obs > qtm::kMaxOps) {
+        std::snprintf(buf, sizeof buf, "qtm_create: at most %d operators in total", qtm::kMaxOps);
+        return fail(nullptr, QTM_ERR_UNSUPPORTED, buf);
+    }
+    if (p->n_c > qtm::kMaxChannels) {
+        std::snprintf(buf, sizeof buf, "qtm_create: at most %d collapse operators", qtm::kMaxChannels);
+        return fail(nullptr, QTM_ERR_UNSUPPORTED, buf);
+    }
+    if (n > qtm::kMaxDimSparse) {
+        std::snprintf(buf, sizeof buf, "qtm_create: dim %d exceeds the largest supported dimension %d", n,
+                      qtm::kMaxDimSparse);
+        return fail(nullptr, QTM_ERR_UNSUPPORTED, buf);
+    }
+
+    qtm_ctx *ctx = new (std::nothrow) qtm_ctx;
+    if (!ctx) return fail(nullptr, QTM_ERR_NOMEM, "qtm_create: out of host memory");
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->alloc = g_allocator;
+    ctx->n = n;
+    ctx->n_c = p->n_c;
+    ctx->n_obs = p->n_obs;
+    ctx->n_t = p->n_t;
+    ctx->precision = p->precision;
+    ctx->flags = p->flags;
+    ctx->max_jumps = (p->flags & QTM_FLAG_RECORD_JUMPS) ? p->max_jumps_recorded : 0;
+    ctx->rtol = p->rtol;
+    ctx->atol = p->atol;
+    ctx->max_steps = p->max_steps;
+    ctx->t.assign(p->t, p->t + p->n_t);
+    const double nrm = std::sqrt(nn);
+    ctx->psi0.resize(n);
+    for (int i = 0; i < n; ++i) ctx->psi0[i] = cd(p->psi0[2 * i] / nrm, p->psi0[2 * i + 1] / nrm);
+    pack(ctx, effective_matrix(H, C));
+    for (const Csr &c : C) pack(ctx, c);
+    for (const Csr &a : A) pack(ctx, a);
+
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e != cudaSuccess) {
+        qtm_status s = cuda_fail(nullptr, e, "qtm_create: cudaGetDevice");
+        delete ctx;
+        return s;
+    }
+    const size_t ib = ctx->ints.size() * sizeof(int), vb = ctx->vals.size() * sizeof(cd);
+    struct {
+        DevBuf *b;
+        size_t bytes;
+    } allocs[] = {{&ctx->d_ints, ib}, {&ctx->d_vals, vb}, {&ctx->d_t, ctx->t.size() * sizeof(double)},
+                  {&ctx->d_psi0, (size_t)n * sizeof(cd)}, {&ctx->d_queue, 16},
+                  {&ctx->d_counters, qtm::kNumCounters * sizeof(unsigned long long)},
+                  {&ctx->d_first_error, 16}};
+    for (cudaEvent_t &ev : ctx->ev)
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) {
+            qtm_status s = cuda_fail(nullptr, e, "qtm_create: cudaEventCreate");
+            destroy_ctx(ctx);
+            return s;
+        }
+    for (auto &al : allocs) {
+        if ((e = dev_alloc(ctx, *al.b, al.bytes)) != cudaSuccess) {
+            qtm_status s = cuda_fail(nullptr, e, "qtm_create: device allocation");
+            destroy_ctx(ctx);
+            return s == QTM_ERR_CUDA && e == cudaErrorMemoryAllocation ? QTM_ERR_NOMEM : s;
+        }
+    }
+    if ((e = cudaMemcpyAsync(ctx->d_ints.p, ctx->ints.data(), ib, cudaMemcpyHostToDevice, ctx->stream)) ||
+        (e = cudaMemcpyAsync(ctx->d_vals.p, ctx->vals.data(), vb, cudaMemcpyHostToDevice, ctx->stream)) ||
+        (e = cudaMemcpyAsync(ctx->d_t.p, ctx->t.data(), ctx->t.size() * sizeof(double),
+                             cudaMemcpyHostToDevice, ctx->stream)) ||
+        (e = cudaMemcpyAsync(ctx->d_psi0.p, ctx->psi0.data(), (size_t)n * sizeof(cd),
+                             cudaMemcpyHostToDevice, ctx->stream)) ||
+        (e = cudaStreamSynchronize(ctx->stream))) {
+        qtm_status s = cuda_fail(nullptr, e, "qtm_create: upload");
+        destroy_ctx(ctx);
+        return s;
+    }
+    *out = ctx;
+    return QTM_OK;
+}
+
+qtm_status qtm_run_range(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64_t seed)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_run: ctx is NULL");
+    ctx->err.clear();
+    if (first < 0 || ntraj < 0) return fail(ctx, QTM_ERR_ARG, "qtm_run: first and ntraj must be >= 0");
+    if (ntraj > ((int64_t)1 << 40)) return fail(ctx, QTM_ERR_ARG, "qtm_run: ntraj too large");
+    const size_t P = (size_t)ctx->n_t * ctx->n_obs;
+    const int S = qtm::reduce_segments(ntraj);
+    cudaError_t e;
+    if ((e = dev_reserve(ctx, ctx->d_out, (size_t)ntraj * P * sizeof(double))) ||
+        (e = dev_reserve(ctx, ctx->d_partial, 2 * (size_t)S * P * sizeof(double))) ||
+        (e = dev_reserve(ctx, ctx->d_stats, 4 * P * sizeof(double))))
+        return cuda_fail(ctx, e, "qtm_run: device allocation");
+    if (ctx->max_jumps > 0) {
+        if ((e = dev_reserve(ctx, ctx->d_njumps, (size_t)ntraj * sizeof(int))) ||
+            (e = dev_reserve(ctx, ctx->d_jump_t, (size_t)ntraj * ctx->max_jumps * sizeof(double))) ||
+            (e = dev_reserve(ctx, ctx->d_jump_ch, (size_t)ntraj * ctx->max_jumps * sizeof(int))))
+            return cuda_fail(ctx, e, "qtm_run: device allocation");
+        if ((e = cudaMemsetAsync(ctx->d_njumps.p, 0, (size_t)ntraj * sizeof(int), ctx->stream)) ||
+            (e = cudaMemsetAsync(ctx->d_jump_t.p, 0xff, (size_t)ntraj * ctx->max_jumps * sizeof(double),
+                                 ctx->stream)) ||
+            (e = cudaMemsetAsync(ctx->d_jump_ch.p, 0xff, (size_t)ntraj * ctx->max_jumps * sizeof(int),
+                                 ctx->stream)))
+            return cuda_fail(ctx, e, "qtm_run: cudaMemsetAsync");
+    }
+    if ((e = cudaMemsetAsync(ctx->d_queue.p, 0, 16, ctx->stream)) ||
+        (e = cudaMemsetAsync(ctx->d_counters.p, 0, qtm::kNumCounters * sizeof(unsigned long long),
+                             ctx->stream)) ||
+        (e = cudaMemsetAsync(ctx->d_first_error.p, 0, 16, ctx->stream)))
+        return cuda_fail(ctx, e, "qtm_run: cudaMemsetAsync");
+
+    if ((e = cudaEventRecord(ctx->ev[0], ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "qtm_run: cudaEventRecord");
+    if (ntraj > 0) {
+        KernelArgs a{};
+        a.n = ctx->n;
+        a.n_c = ctx->n_c;
+        a.n_obs = ctx->n_obs;
+        a.n_t = ctx->n_t;
+        a.ints = (const int *)ctx->d_ints.p;
+        a.vals = ctx->d_vals.p;
+        a.n_ints = (int)ctx->ints.size();
+        a.n_vals = (int)ctx->vals.size();
+        for (size_t i = 0; i < ctx->ops.size(); ++i) a.op[i] = ctx->ops[i];
+        a.t = (const double *)ctx->d_t.p;
+        a.psi0 = ctx->d_psi0.p;
+        a.rtol = ctx->rtol;
+        a.atol = ctx->atol;
+        a.max_steps = ctx->max_steps;
+        a.seed = seed;
+        a.traj0 = first;
+        a.ntraj = ntraj;
+        a.queue = (unsigned long long *)ctx->d_queue.p;
+        a.out = (double *)ctx->d_out.p;
+        a.counters = (unsigned long long *)ctx->d_counters.p;
+        a.first_error = (int *)ctx->d_first_error.p;
+        a.max_jumps = ctx->max_jumps;
+        a.n_jumps = (int *)ctx->d_njumps.p;
+        a.jump_t = (double *)ctx->d_jump_t.p;
+        a.jump_ch = (int *)ctx->d_jump_ch.p;
+        e = qtm::launch_mcwf_c128(a, ctx->stream, &ctx->info);
+        if (e == cudaErrorInvalidValue)
+            return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_run: no trajectory kernel fits this problem");
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "qtm_run: trajectory kernel launch");
+    }
+    if ((e = cudaEventRecord(ctx->ev[1], ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "qtm_run: cudaEventRecord");
+    double *st = (double *)ctx->d_stats.p;
+    e = qtm::launch_ensemble_reduce((const double *)ctx->d_out.p, ntraj, (int)P, (double *)ctx->d_partial.p,
+                                    st, st + P, st + 2 * P, st + 3 * P, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qtm_run: ensemble reduction launch");
+    if ((e = cudaEventRecord(ctx->ev[2], ctx->stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "qtm_run: cudaEventRecord");
+    ctx->timed = true;
+    ctx->last_ntraj = ntraj;
+    return QTM_OK;
+}
+
+qtm_status qtm_run(qtm_ctx *ctx, int64_t ntraj, uint64_t seed) { return qtm_run_range(ctx, 0, ntraj, seed); }
+
+static qtm_status sync_and_status(qtm_ctx *ctx)
+{
+    if (ctx->last_ntraj < 0) return fail(ctx, QTM_ERR_STATE, "no qtm_run on this context yet");
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamSynchronize");
+    int first = 0;
+    e = cudaMemcpy(&first, ctx->d_first_error.p, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy");
+    if (first != 0) {
+        char buf[128];
+        std::snprintf(buf, sizeof buf, "a trajectory stopped with %s", qtm_status_string((qtm_status)first));
+        return fail(ctx, (qtm_status)first, buf);
+    }
+    return QTM_OK;
+}
+
+static qtm_status copy_stats(qtm_ctx *ctx, int which, double *dst)
+{
+    const size_t P = (size_t)ctx->n_t * ctx->n_obs;
+    if (P == 0) return QTM_OK;
+    cudaError_t e = cudaMemcpy(dst, (double *)ctx->d_stats.p + (size_t)which * P, P * sizeof(double),
+                               cudaMemcpyDeviceToHost);
+    return e == cudaSuccess ? QTM_OK : cuda_fail(ctx, e, "cudaMemcpy");
+}
+
+qtm_status qtm_expect(qtm_ctx *ctx, double *mean, double *stderr_out)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_expect: ctx is NULL");
+    if (!mean) return fail(ctx, QTM_ERR_ARG, "qtm_expect: mean is NULL");
+    qtm_status run_status = sync_and_status(ctx);
+    if (run_status == QTM_ERR_STATE || run_status == QTM_ERR_CUDA) return run_status;
+    qtm_status s = copy_stats(ctx, 2, mean);
+    if (s) return s;
+    if (stderr_out && (s = copy_stats(ctx, 3, stderr_out))) return s;
+    return run_status;
+}
+
+qtm_status qtm_sums(qtm_ctx *ctx, double *sum, double *sumsq, int64_t *count)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_sums: ctx is NULL");
+    if (!sum || !sumsq || !count) return fail(ctx, QTM_ERR_ARG, "qtm_sums: NULL output");
+    qtm_status run_status = sync_and_status(ctx);
+    if (run_status == QTM_ERR_STATE || run_status == QTM_ERR_CUDA) return run_status;
+    qtm_status s;
+    if ((s = copy_stats(ctx, 0, sum)) || (s = copy_stats(ctx, 1, sumsq))) return s;
+    *count = ctx->last_ntraj;
+    return run_status;
+}
+
+qtm_status qtm_sums_device(qtm_ctx *ctx, double *sum_dev, double *sumsq_dev)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_sums_device: ctx is NULL");
+    if (!sum_dev || !sumsq_dev) return fail(ctx, QTM_ERR_ARG, "qtm_sums_device: NULL output");
+    if (ctx->last_ntraj < 0) return fail(ctx, QTM_ERR_STATE, "no qtm_run on this context yet");
+    const size_t P = (size_t)ctx->n_t * ctx->n_obs;
+    if (P == 0) return QTM_OK;
+    const double *st = (const double *)ctx->d_stats.p;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(sum_dev, st, P * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream)) ||
+        (e = cudaMemcpyAsync(sumsq_dev, st + P, P * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream)))
+        return cuda_fail(ctx, e, "qtm_sums_device: cudaMemcpyAsync");
+    return QTM_OK;
+}
+
+qtm_status qtm_traj_expect(qtm_ctx *ctx, double *out)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_traj_expect: ctx is NULL");
+    if (!out) return fail(ctx, QTM_ERR_ARG, "qtm_traj_expect: out is NULL");
+    qtm_status run_status = sync_and_status(ctx);
+    if (run_status == QTM_ERR_STATE || run_status == QTM_ERR_CUDA) return run_status;
+    const size_t bytes = (size_t)ctx->last_ntraj * ctx->n_t * ctx->n_obs * sizeof(double);
+    if (bytes) {
+        cudaError_t e = cudaMemcpy(out, ctx->d_out.p, bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy");
+    }
+    return run_status;
+}
+
+qtm_status qtm_jumps(qtm_ctx *ctx, int32_t *n_jumps, double *jump_t, int32_t *jump_ch)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_jumps: ctx is NULL");
+    if (ctx->max_jumps == 0) return fail(ctx, QTM_ERR_STATE, "qtm_jumps: context was created without QTM_FLAG_RECORD_JUMPS");
+    if (!n_jumps || !jump_t || !jump_ch) return fail(ctx, QTM_ERR_ARG, "qtm_jumps: NULL output");
+    qtm_status run_status = sync_and_status(ctx);
+    if (run_status == QTM_ERR_STATE || run_status == QTM_ERR_CUDA) return run_status;
+    const size_t nt = (size_t)ctx->last_ntraj;
+    if (nt) {
+        cudaError_t e;
+        if ((e = cudaMemcpy(n_jumps, ctx->d_njumps.p, nt * sizeof(int), cudaMemcpyDeviceToHost)) ||
+            (e = cudaMemcpy(jump_t, ctx->d_jump_t.p, nt * ctx->max_jumps * sizeof(double), cudaMemcpyDeviceToHost)) ||
+            (e = cudaMemcpy(jump_ch, ctx->d_jump_ch.p, nt * ctx->max_jumps * sizeof(int), cudaMemcpyDeviceToHost)))
+            return cuda_fail(ctx, e, "cudaMemcpy");
+    }
+    return run_status;
+}
+
+qtm_status qtm_stats(qtm_ctx *ctx, qtm_stats_t *out)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_stats: ctx is NULL");
+    if (!out) return fail(ctx, QTM_ERR_ARG, "qtm_stats: out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    qtm_status run_status = sync_and_status(ctx);
+    if (run_status == QTM_ERR_STATE || run_status == QTM_ERR_CUDA) return run_status;
+    unsigned long long c[qtm::kNumCounters];
+    cudaError_t e = cudaMemcpy(c, ctx->d_counters.p, sizeof c, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy");
+    out->trajectories = ctx->last_ntraj;
+    out->accepted = (int64_t)c[qtm::kAccepted];
+    out->rejected = (int64_t)c[qtm::kRejected];
+    out->rhs_evals = (int64_t)c[qtm::kRhs];
+    out->jumps = (int64_t)c[qtm::kJumps];
+    out->root_iters = (int64_t)c[qtm::kRootIters];
+    out->failed = (int64_t)c[qtm::kFailed];
+    out->first_error = (int32_t)run_status;
+    out->kernel_group = ctx->info.group;
+    out->kernel_rows = ctx->info.rows;
+    out->grid = ctx->info.grid;
+    out->block = ctx->info.block;
+    if (ctx->timed) {
+        float ms = 0.f;
+        if (ctx->last_ntraj > 0 && cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]) == cudaSuccess)
+            out->kernel_ms = ms;
+        if (cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]) == cudaSuccess) out->reduce_ms = ms;
+    }
+    return QTM_OK;
+}
+
+void qtm_destroy(qtm_ctx *ctx) { destroy_ctx(ctx); }
+
+}  // extern "C"

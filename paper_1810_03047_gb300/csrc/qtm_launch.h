@@ -1,0 +1,68 @@
+// qtm_launch.h -- arguments of the trajectory kernels, shared by the host side of
+// the library (qtm_api.cpp) and the CUDA translation units that launch them.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace qtm {
+
+constexpr int kMaxOps = 64;        // M + collapse operators + observables
+constexpr int kMaxChannels = 48;   // collapse operators per problem
+
+// Offsets of one CSR operator inside the packed operator blob.
+struct OpOffsets {
+    int rp;   // row_ptr (n + 1 ints) in the int array
+    int ci;   // column indices in the int array
+    int val;  // values in the value array (complex elements)
+};
+
+struct KernelArgs {
+    int n, n_c, n_obs, n_t;
+    // packed operators: op[0] = M = -i H_eff, op[1..n_c] = C_n, op[1+n_c..] = A_k
+    const int *ints;
+    const void *vals;         // cpx<V> elements of the kernel's value type
+    int n_ints, n_vals;
+    OpOffsets op[kMaxOps];
+    const double *t;          // n_t output times
+    const void *psi0;         // n elements of cpx<V>, normalised
+    double rtol, atol;
+    long long max_steps;
+    unsigned long long seed;
+    long long traj0, ntraj;   // global id of local trajectory 0; trajectories in this launch
+    unsigned long long *queue;     // work counter (zeroed before launch)
+    double *out;              // [ntraj][n_t][n_obs]
+    unsigned long long *counters;  // accepted, rejected, rhs, jumps, root iterations, failed
+    int *first_error;         // first non-zero per-trajectory status (zeroed before launch)
+    int max_jumps;            // jump records per trajectory (0 = none)
+    int *n_jumps;             // [ntraj]
+    double *jump_t;           // [ntraj][max_jumps]
+    int *jump_ch;             // [ntraj][max_jumps]
+    int smem_vals_offset;     // byte offset of the value array in dynamic shared memory
+    int smem_ybuf_offset;     // byte offset of the per-trajectory exchange buffers
+};
+
+enum CounterIndex { kAccepted = 0, kRejected, kRhs, kJumps, kRootIters, kFailed, kNumCounters };
+
+struct LaunchInfo {
+    int group, rows, grid, block;
+    size_t smem;
+};
+
+// Largest dimension the register-resident trajectory kernels handle.
+constexpr int kMaxDimSparse = 64;
+
+// FP64 (complex128) trajectory kernel, CSR operators.  Chooses lanes per
+// trajectory and rows per lane from args.n; returns cudaErrorInvalidValue when
+// no instantiation fits.
+cudaError_t launch_mcwf_c128(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+
+// Ensemble reduction of out[ntraj][P] into sums, sums of squares, mean and
+// standard error, in a fixed summation order (bitwise reproducible).
+// partial must hold 2 * S * P doubles for S = reduce_segments(ntraj).
+int reduce_segments(long long ntraj);
+cudaError_t launch_ensemble_reduce(const double *out, long long ntraj, int P, double *partial,
+                                   double *sum, double *sumsq, double *mean, double *se,
+                                   cudaStream_t stream);
+
+}  // namespace qtm

@@ -1,0 +1,310 @@
+"""Thin ctypes binding of the C ABI in ``include/qtm.h`` (same function names).
+
+Argument marshalling only: every step of the trajectory method runs in the CUDA
+library ``_build/libqtm.so``.  There is no fallback -- if the library cannot be
+built or loaded, every call raises.  PyTorch is used for device memory (the
+library allocates through the PyTorch caching allocator once
+``use_torch_allocator()`` is called) and for the CUDA stream.
+"""
+
+from __future__ import annotations
+
+import ctypes as ct
+import threading
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+QTM_OK = 0
+QTM_ERR_ARG = 1
+QTM_ERR_CUDA = 2
+QTM_ERR_NOMEM = 3
+QTM_ERR_MAXSTEPS = 4
+QTM_ERR_STEPSIZE = 5
+QTM_ERR_NONFINITE = 6
+QTM_ERR_NO_CHANNEL = 7
+QTM_ERR_TIMEOUT = 8
+QTM_ERR_STATE = 9
+QTM_ERR_UNSUPPORTED = 10
+
+QTM_FORMAT_DENSE = 0
+QTM_FORMAT_CSR = 1
+QTM_PREC_C128 = 0
+QTM_FLAG_RECORD_JUMPS = 1
+
+# every entry point declared in include/qtm.h
+EXPORTS = ["qtm_set_allocator", "qtm_create", "qtm_run", "qtm_run_range", "qtm_expect", "qtm_sums",
+           "qtm_sums_device",
+           "qtm_traj_expect", "qtm_jumps", "qtm_stats", "qtm_last_error", "qtm_status_string",
+           "qtm_destroy", "qtm_version"]
+
+
+class QtmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_status_name(status)}: {message}")
+        self.status = status
+
+
+class QtmOp(ct.Structure):
+    _fields_ = [("n", ct.c_int32), ("format", ct.c_int32), ("row_ptr", ct.POINTER(ct.c_int32)),
+                ("col_ind", ct.POINTER(ct.c_int32)), ("values", ct.POINTER(ct.c_double)),
+                ("nnz", ct.c_int64)]
+
+
+class QtmProblem(ct.Structure):
+    _fields_ = [("dim", ct.c_int32), ("H", QtmOp), ("n_c", ct.c_int32), ("C", ct.POINTER(QtmOp)),
+                ("n_obs", ct.c_int32), ("A", ct.POINTER(QtmOp)), ("psi0", ct.POINTER(ct.c_double)),
+                ("n_t", ct.c_int32), ("t", ct.POINTER(ct.c_double)), ("rtol", ct.c_double),
+                ("atol", ct.c_double), ("precision", ct.c_int32), ("max_steps", ct.c_int64),
+                ("flags", ct.c_int32), ("max_jumps_recorded", ct.c_int32)]
+
+
+class QtmStats(ct.Structure):
+    _fields_ = [("trajectories", ct.c_int64), ("accepted", ct.c_int64), ("rejected", ct.c_int64),
+                ("rhs_evals", ct.c_int64), ("jumps", ct.c_int64), ("root_iters", ct.c_int64),
+                ("failed", ct.c_int64), ("first_error", ct.c_int32), ("kernel_group", ct.c_int32),
+                ("kernel_rows", ct.c_int32), ("grid", ct.c_int32), ("block", ct.c_int32),
+                ("reserved", ct.c_int32), ("kernel_ms", ct.c_double), ("reduce_ms", ct.c_double)]
+
+
+ALLOC_FN = ct.CFUNCTYPE(ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_void_p)
+FREE_FN = ct.CFUNCTYPE(None, ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_void_p)
+
+_lib = None
+_lock = threading.Lock()
+_keep_alive = []
+
+
+def lib():
+    """Builds (if sources changed) and loads libqtm.so; raises if either fails."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ct.CDLL(path)
+            L.qtm_create.argtypes = [ct.POINTER(QtmProblem), ct.c_void_p, ct.POINTER(ct.c_void_p)]
+            L.qtm_run.argtypes = [ct.c_void_p, ct.c_int64, ct.c_uint64]
+            L.qtm_run_range.argtypes = [ct.c_void_p, ct.c_int64, ct.c_int64, ct.c_uint64]
+            L.qtm_expect.argtypes = [ct.c_void_p, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
+            L.qtm_sums.argtypes = [ct.c_void_p, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double),
+                                   ct.POINTER(ct.c_int64)]
+            L.qtm_sums_device.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p]
+            L.qtm_traj_expect.argtypes = [ct.c_void_p, ct.POINTER(ct.c_double)]
+            L.qtm_jumps.argtypes = [ct.c_void_p, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_double),
+                                    ct.POINTER(ct.c_int32)]
+            L.qtm_stats.argtypes = [ct.c_void_p, ct.POINTER(QtmStats)]
+            L.qtm_last_error.argtypes = [ct.c_void_p]
+            L.qtm_last_error.restype = ct.c_char_p
+            L.qtm_status_string.argtypes = [ct.c_int]
+            L.qtm_status_string.restype = ct.c_char_p
+            L.qtm_destroy.argtypes = [ct.c_void_p]
+            L.qtm_destroy.restype = None
+            L.qtm_version.restype = ct.c_char_p
+            L.qtm_set_allocator.argtypes = [ALLOC_FN, FREE_FN, ct.c_void_p]
+            for name in ("qtm_create", "qtm_run", "qtm_run_range", "qtm_expect", "qtm_sums", "qtm_sums_device",
+                         "qtm_traj_expect", "qtm_jumps", "qtm_stats", "qtm_set_allocator"):
+                getattr(L, name).restype = ct.c_int
+            _lib = L
+        return _lib
+
+
+def _status_name(status: int) -> str:
+    try:
+        return lib().qtm_status_string(int(status)).decode()
+    except Exception:  # pragma: no cover - only when the library itself is unusable
+        return f"status {status}"
+
+
+def qtm_version() -> str:
+    return lib().qtm_version().decode()
+
+
+def qtm_status_string(status: int) -> str:
+    return _status_name(status)
+
+
+def qtm_last_error(ctx: Optional["Ctx"] = None) -> str:
+    return lib().qtm_last_error(ctx.handle if ctx is not None else None).decode()
+
+
+def _check(status: int, ctx=None):
+    if status != QTM_OK:
+        raise QtmError(status, qtm_last_error(ctx))
+
+
+def use_torch_allocator():
+    """Routes the library's device allocations through the PyTorch caching allocator."""
+    import torch
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+        except Exception:
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    cb = (ALLOC_FN(_alloc), FREE_FN(_free))
+    _keep_alive.append(cb)
+    _check(lib().qtm_set_allocator(cb[0], cb[1], None))
+
+
+def use_default_allocator():
+    _check(lib().qtm_set_allocator(ALLOC_FN(), FREE_FN(), None))
+
+
+def current_stream():
+    """The current PyTorch CUDA stream as a raw cudaStream_t (int)."""
+    import torch
+    return int(torch.cuda.current_stream().cuda_stream)
+
+
+class Ctx:
+    """A library context plus the shapes needed to size host output arrays."""
+
+    def __init__(self, handle, n_t, n_obs, max_jumps):
+        self.handle = handle
+        self.n_t = n_t
+        self.n_obs = n_obs
+        self.max_jumps = max_jumps
+        self.last_ntraj = None
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                qtm_destroy(self)
+            except Exception:
+                pass
+
+
+def _op(m, dense: bool, keep: list) -> QtmOp:
+    op = QtmOp()
+    n = int(m.shape[0])
+    op.n = n
+    if dense:
+        d = np.ascontiguousarray(m.toarray() if hasattr(m, "toarray") else m, dtype=np.complex128)
+        v = d.view(np.float64).ravel()
+        keep.append(v)
+        op.format = QTM_FORMAT_DENSE
+        op.values = v.ctypes.data_as(ct.POINTER(ct.c_double))
+        op.nnz = 0
+        return op
+    m = m.tocsr()
+    rp = np.ascontiguousarray(m.indptr, dtype=np.int32)
+    ci = np.ascontiguousarray(m.indices, dtype=np.int32)
+    v = np.ascontiguousarray(m.data, dtype=np.complex128).view(np.float64)
+    keep += [rp, ci, v]
+    op.format = QTM_FORMAT_CSR
+    op.row_ptr = rp.ctypes.data_as(ct.POINTER(ct.c_int32))
+    op.col_ind = ci.ctypes.data_as(ct.POINTER(ct.c_int32))
+    op.values = v.ctypes.data_as(ct.POINTER(ct.c_double))
+    op.nnz = int(m.nnz)
+    return op
+
+
+def make_problem(prob, precision: int = QTM_PREC_C128, record_jumps: int = 0):
+    """Marshals a problem object (H, C, A, psi0, t, rtol, atol, max_steps, dense)."""
+    keep = []
+    dense = bool(getattr(prob, "dense", False))
+    p = QtmProblem()
+    p.dim = int(prob.H.shape[0])
+    p.H = _op(prob.H, dense, keep)
+    cs = [_op(c, dense, keep) for c in prob.C]
+    as_ = [_op(a, dense, keep) for a in prob.A]
+    carr = (QtmOp * max(1, len(cs)))(*cs)
+    aarr = (QtmOp * max(1, len(as_)))(*as_)
+    keep += [carr, aarr]
+    p.n_c = len(cs)
+    p.C = ct.cast(carr, ct.POINTER(QtmOp))
+    p.n_obs = len(as_)
+    p.A = ct.cast(aarr, ct.POINTER(QtmOp))
+    psi = np.ascontiguousarray(np.asarray(prob.psi0, dtype=np.complex128)).view(np.float64)
+    t = np.ascontiguousarray(np.asarray(prob.t, dtype=np.float64))
+    keep += [psi, t]
+    p.psi0 = psi.ctypes.data_as(ct.POINTER(ct.c_double))
+    p.n_t = len(t)
+    p.t = t.ctypes.data_as(ct.POINTER(ct.c_double))
+    p.rtol = float(prob.rtol)
+    p.atol = float(prob.atol)
+    p.precision = int(precision)
+    p.max_steps = int(getattr(prob, "max_steps", 1_000_000))
+    p.flags = QTM_FLAG_RECORD_JUMPS if record_jumps else 0
+    p.max_jumps_recorded = int(record_jumps)
+    return p, keep
+
+
+def qtm_create(prob, stream=None, precision: int = QTM_PREC_C128, record_jumps: int = 0) -> Ctx:
+    p, keep = make_problem(prob, precision, record_jumps)
+    h = ct.c_void_p()
+    _check(lib().qtm_create(ct.byref(p), ct.c_void_p(stream or 0), ct.byref(h)))
+    return Ctx(h.value, len(prob.t), len(prob.A), int(record_jumps))
+
+
+def qtm_run(ctx: Ctx, ntraj: int, seed: int):
+    _check(lib().qtm_run(ctx.handle, int(ntraj), int(seed)), ctx)
+    ctx.last_ntraj = int(ntraj)
+
+
+def qtm_run_range(ctx: Ctx, first: int, ntraj: int, seed: int):
+    _check(lib().qtm_run_range(ctx.handle, int(first), int(ntraj), int(seed)), ctx)
+    ctx.last_ntraj = int(ntraj)
+
+
+def _dp(a):
+    return a.ctypes.data_as(ct.POINTER(ct.c_double))
+
+
+def qtm_expect(ctx: Ctx, check: bool = True):
+    """(mean, stderr), each of shape (n_t, n_obs)."""
+    mean = np.zeros((ctx.n_t, ctx.n_obs))
+    se = np.zeros((ctx.n_t, ctx.n_obs))
+    st = lib().qtm_expect(ctx.handle, _dp(mean), _dp(se))
+    if check:
+        _check(st, ctx)
+    return mean, se
+
+
+def qtm_sums(ctx: Ctx):
+    s = np.zeros((ctx.n_t, ctx.n_obs))
+    s2 = np.zeros((ctx.n_t, ctx.n_obs))
+    n = ct.c_int64()
+    _check(lib().qtm_sums(ctx.handle, _dp(s), _dp(s2), ct.byref(n)), ctx)
+    return s, s2, n.value
+
+
+def qtm_sums_device(ctx: Ctx, sum_dev_ptr: int, sumsq_dev_ptr: int):
+    """Asynchronous copy of the run's FP64 sums into caller-owned device buffers."""
+    _check(lib().qtm_sums_device(ctx.handle, ct.c_void_p(sum_dev_ptr), ct.c_void_p(sumsq_dev_ptr)), ctx)
+
+
+def qtm_traj_expect(ctx: Ctx, check: bool = True):
+    out = np.zeros((ctx.last_ntraj or 0, ctx.n_t, ctx.n_obs))
+    st = lib().qtm_traj_expect(ctx.handle, _dp(out))
+    if check:
+        _check(st, ctx)
+    return out
+
+
+def qtm_jumps(ctx: Ctx):
+    nt = ctx.last_ntraj or 0
+    nj = np.zeros(nt, np.int32)
+    jt = np.zeros((nt, max(1, ctx.max_jumps)))
+    jc = np.zeros((nt, max(1, ctx.max_jumps)), np.int32)
+    _check(lib().qtm_jumps(ctx.handle, nj.ctypes.data_as(ct.POINTER(ct.c_int32)), _dp(jt),
+                           jc.ctypes.data_as(ct.POINTER(ct.c_int32))), ctx)
+    return nj, jt, jc
+
+
+def qtm_stats(ctx: Ctx) -> dict:
+    s = QtmStats()
+    _check(lib().qtm_stats(ctx.handle, ct.byref(s)), ctx)
+    return {name: getattr(s, name) for name, _ in QtmStats._fields_}
+
+
+def qtm_destroy(ctx: Ctx):
+    if ctx.handle:
+        lib().qtm_destroy(ctx.handle)
+        ctx.handle = None
