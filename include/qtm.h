@@ -180,6 +180,45 @@ qtm_status qtm_sums(qtm_ctx *ctx, double *sum, double *sumsq, int64_t *count);
  * a host round trip. */
 qtm_status qtm_sums_device(qtm_ctx *ctx, double *sum_dev, double *sumsq_dev);
 
+/* Maximum scratch of qtm_ensemble_reduce_static, in doubles (4 MiB), and the
+ * largest n_values it accepts. */
+#define QTM_STATIC_SCRATCH_DOUBLES (1 << 19)
+#define QTM_STATIC_MAX_VALUES (QTM_STATIC_SCRATCH_DOUBLES / 2)
+
+/* Ensemble mean and standard error of per-trajectory values the caller already
+ * holds on the device, computed without allocating any device memory.  The
+ * paper has no counterpart: it exists for callers that may not let a library
+ * allocate -- for example a host framework whose memory planner owns every
+ * device buffer and only lends the library its inputs and outputs, or a
+ * service that fixes its device footprint at start-up and must not grow it
+ * while it runs.  qtm_run / qtm_expect allocate through their context; this
+ * call does not (no cudaMalloc, no allocator hook, no library that allocates).
+ *
+ *   values_dev  DEVICE pointer, [ntraj][n_values] doubles (e.g. the layout of
+ *               qtm_traj_expect: n_values = n_t * n_obs), read only.
+ *   ntraj       >= 0 trajectories.
+ *   n_values    1 .. QTM_STATIC_MAX_VALUES values per trajectory; larger sizes
+ *               return QTM_ERR_ARG with a message in qtm_last_error(NULL).
+ *   sum_dev, sumsq_dev, mean_dev, stderr_dev
+ *               DEVICE pointers to n_values doubles each, written with the same
+ *               quantities as qtm_sums and qtm_expect (sample variance, n - 1).
+ *   cuda_stream the stream the work is ordered on (NULL = legacy default).
+ *
+ * Scratch: the per-segment partial sums live in one array of
+ * QTM_STATIC_SCRATCH_DOUBLES doubles that is part of the library's device
+ * image, so every GPU that loads the library holds those 4 MiB until the
+ * process exits.  Every call on a device uses the same array: calls whose work
+ * overlaps on the GPU (different streams without ordering between them) race
+ * on it and give wrong results; order them on one stream.  Each call writes
+ * every scratch element it reads before reading it, so nothing needs clearing
+ * between calls.  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current), so make that first
+ * call before any stream capture on that device.  The call is asynchronous;
+ * results are ready when the stream reaches it. */
+qtm_status qtm_ensemble_reduce_static(const double *values_dev, int64_t ntraj, int32_t n_values,
+                                      double *sum_dev, double *sumsq_dev, double *mean_dev,
+                                      double *stderr_dev, void *cuda_stream);
+
 /* Per-trajectory values of the last run, [traj][j][k] (ntraj * n_t * n_obs doubles). */
 qtm_status qtm_traj_expect(qtm_ctx *ctx, double *out);
 

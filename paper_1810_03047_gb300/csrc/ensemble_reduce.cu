@@ -6,6 +6,9 @@
 // partial sums are added in segment order.  The standard error takes a second
 // pass over the deviations from the mean.  No floating-point atomics are used,
 // so the result is bitwise reproducible for a given trajectory count.
+#include <mutex>
+
+#include "../../include/qtm.h"
 #include "qtm_launch.h"
 
 namespace qtm {
@@ -117,3 +120,86 @@ cudaError_t launch_ensemble_reduce(const double *out, long long ntraj, int P, do
 }
 
 }  // namespace qtm
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant: the same four kernels, with the partial sums in a
+// fixed array of the library's device image instead of context memory.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+static __device__ __align__(256) double g_static_scratch[QTM_STATIC_SCRATCH_DOUBLES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_scratch_mutex;
+double *g_static_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device, looked up once per
+// device (host code cannot use the symbol itself as a device pointer).
+cudaError_t static_scratch(double **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_static_scratch_mutex);
+    if (!g_static_scratch_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess) return e;
+        g_static_scratch_addr[dev] = static_cast<double *>(p);
+    }
+    *out = g_static_scratch_addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" qtm_status qtm_ensemble_reduce_static(const double *values_dev, int64_t ntraj, int32_t n_values,
+                                                 double *sum_dev, double *sumsq_dev, double *mean_dev,
+                                                 double *stderr_dev, void *cuda_stream)
+{
+    using namespace qtm;
+    if (ntraj < 0) {
+        set_last_error("qtm_ensemble_reduce_static: ntraj must be >= 0");
+        return QTM_ERR_ARG;
+    }
+    if (n_values < 1 || n_values > QTM_STATIC_MAX_VALUES) {
+        set_last_error("qtm_ensemble_reduce_static: n_values must be in 1..QTM_STATIC_MAX_VALUES (262144); "
+                       "the fixed scratch array cannot hold the partial sums of more");
+        return QTM_ERR_ARG;
+    }
+    if ((ntraj > 0 && !values_dev) || !sum_dev || !sumsq_dev || !mean_dev || !stderr_dev) {
+        set_last_error("qtm_ensemble_reduce_static: NULL buffer");
+        return QTM_ERR_ARG;
+    }
+    double *scratch = nullptr;
+    cudaError_t e = static_scratch(&scratch);
+    if (e != cudaSuccess) {
+        set_last_error("qtm_ensemble_reduce_static: cudaGetSymbolAddress of the scratch array failed");
+        return QTM_ERR_CUDA;
+    }
+    // Segments: as in the context path, but never more than the scratch holds
+    // (pass 1 keeps two partials per segment and value).
+    const long long P = n_values;
+    long long max_seg_count = QTM_STATIC_SCRATCH_DOUBLES / (2 * P);
+    if (max_seg_count > kMaxSegments) max_seg_count = kMaxSegments;
+    long long seg = kSegLen;
+    while ((ntraj + seg - 1) / seg > max_seg_count) seg *= 2;
+    long long S = (ntraj + seg - 1) / seg;
+    if (S < 1) S = 1;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    double *psum = scratch, *psq = scratch + S * P;
+    const dim3 grid_seg((unsigned)((P + kThreads - 1) / kThreads), (unsigned)S);
+    const unsigned grid_p = (unsigned)((P + kThreads - 1) / kThreads);
+    segment_sums<<<grid_seg, kThreads, 0, stream>>>(values_dev, ntraj, (int)P, seg, psum, psq);
+    combine_sums<<<grid_p, kThreads, 0, stream>>>(psum, psq, (int)S, (int)P, ntraj, sum_dev, sumsq_dev,
+                                                  mean_dev);
+    segment_devs<<<grid_seg, kThreads, 0, stream>>>(values_dev, ntraj, (int)P, seg, mean_dev, psum);
+    combine_devs<<<grid_p, kThreads, 0, stream>>>(psum, (int)S, (int)P, ntraj, stderr_dev);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+        set_last_error("qtm_ensemble_reduce_static: kernel launch failed");
+        return QTM_ERR_CUDA;
+    }
+    return QTM_OK;
+}

@@ -263,6 +263,10 @@ void destroy_ctx(qtm_ctx *ctx)
 
 }  // namespace
 
+namespace qtm {
+void set_last_error(const char *msg) { g_create_error = msg; }
+}  // namespace qtm
+
 extern "C" {
 
 const char *qtm_version(void) { return "0.1.0 sm_103a"; }

@@ -65,4 +65,7 @@ cudaError_t launch_ensemble_reduce(const double *out, long long ntraj, int P, do
                                    double *sum, double *sumsq, double *mean, double *se,
                                    cudaStream_t stream);
 
+// Sets the message returned by qtm_last_error(NULL).
+void set_last_error(const char *msg);
+
 }  // namespace qtm

@@ -38,7 +38,7 @@ QTM_FLAG_RECORD_JUMPS = 1
 EXPORTS = ["qtm_set_allocator", "qtm_create", "qtm_run", "qtm_run_range", "qtm_expect", "qtm_sums",
            "qtm_sums_device",
            "qtm_traj_expect", "qtm_jumps", "qtm_stats", "qtm_last_error", "qtm_status_string",
-           "qtm_destroy", "qtm_version"]
+           "qtm_destroy", "qtm_version", "qtm_ensemble_reduce_static"]
 
 
 class QtmError(RuntimeError):
@@ -103,6 +103,9 @@ def lib():
             L.qtm_destroy.restype = None
             L.qtm_version.restype = ct.c_char_p
             L.qtm_set_allocator.argtypes = [ALLOC_FN, FREE_FN, ct.c_void_p]
+            L.qtm_ensemble_reduce_static.argtypes = [ct.c_void_p, ct.c_int64, ct.c_int32, ct.c_void_p,
+                                                     ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]
+            L.qtm_ensemble_reduce_static.restype = ct.c_int
             for name in ("qtm_create", "qtm_run", "qtm_run_range", "qtm_expect", "qtm_sums", "qtm_sums_device",
                          "qtm_traj_expect", "qtm_jumps", "qtm_stats", "qtm_set_allocator"):
                 getattr(L, name).restype = ct.c_int
@@ -302,6 +305,17 @@ def qtm_stats(ctx: Ctx) -> dict:
     s = QtmStats()
     _check(lib().qtm_stats(ctx.handle, ct.byref(s)), ctx)
     return {name: getattr(s, name) for name, _ in QtmStats._fields_}
+
+
+def qtm_ensemble_reduce_static(values_dev: int, ntraj: int, n_values: int, sum_dev: int, sumsq_dev: int,
+                               mean_dev: int, stderr_dev: int, stream: int = 0):
+    """Mean / standard error of device-resident per-trajectory values with no device
+    allocation (scratch is a fixed 4 MiB array inside the library; see qtm.h).
+    All pointers are raw device addresses; the call is asynchronous on ``stream``."""
+    _check(lib().qtm_ensemble_reduce_static(ct.c_void_p(values_dev), int(ntraj), int(n_values),
+                                            ct.c_void_p(sum_dev), ct.c_void_p(sumsq_dev),
+                                            ct.c_void_p(mean_dev), ct.c_void_p(stderr_dev),
+                                            ct.c_void_p(stream or 0)))
 
 
 def qtm_destroy(ctx: Ctx):
