@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="c128", choices=["c128", "df64", "c64"],
+                    help="trajectory arithmetic: complex128, double-float or complex64")
     return ap.parse_args()
 
 
@@ -226,7 +228,8 @@ def main():
     first = rank * ntraj
     stream = torch.cuda.current_stream()
     Q.use_torch_allocator()
-    ctx = Q.qtm_create(prob, stream=int(stream.cuda_stream))
+    prec = {"c128": Q.QTM_PREC_C128, "df64": Q.QTM_PREC_DF64, "c64": Q.QTM_PREC_C64}[args.precision]
+    ctx = Q.qtm_create(prob, stream=int(stream.cuda_stream), precision=prec)
     P = len(prob.t) * len(prob.A)
     sums = torch.zeros(2 * P, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
@@ -286,7 +289,7 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        c2 = Q.qtm_create(prob, stream=int(stream.cuda_stream))
+        c2 = Q.qtm_create(prob, stream=int(stream.cuda_stream), precision=prec)
         Q.qtm_run_range(c2, first, ntraj, prob.seed)
         Q.qtm_expect(c2)
         Q.qtm_destroy(c2)

@@ -80,9 +80,18 @@ typedef enum {
 
 enum { QTM_FORMAT_DENSE = 0, QTM_FORMAT_CSR = 1 };
 
-/* Arithmetic of the trajectory integration. */
+/* Arithmetic of the trajectory integration.  In every mode the time, step size,
+ * crossing test, jump-time root find and ensemble reduction are FP64. */
 enum {
-    QTM_PREC_C128 = 0   /* complex128 state, operators and stage products (FP64 throughout) */
+    QTM_PREC_C128 = 0,  /* complex128 state, operators and stage products (FP64 throughout) */
+    QTM_PREC_C64 = 1,   /* complex64 state, operators and stage products; norms and inner
+                           products accumulated in double-float (about 48 bits); the
+                           step-size control in FP32.  Faster, but a trajectory's jump
+                           times move by about the FP32 rounding of its state */
+    QTM_PREC_DF64 = 3   /* double-float: every real is a pair of FP32 numbers hi + lo
+                           (about 48 significant bits) and every product and sum is
+                           error-free-transformed on the FP32 pipe; matches complex128
+                           to round-off while running on GB300's much wider FP32 units */
 };
 
 /* qtm_problem.flags */

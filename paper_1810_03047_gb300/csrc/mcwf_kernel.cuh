@@ -2,18 +2,26 @@
 // paper for a whole ensemble in one persistent launch.
 //
 // Mapping onto the GPU.  G consecutive lanes of a warp own one trajectory; lane
-// gl keeps rows gl, gl+G, ... (R of them) of every Dormand-Prince vector -- the
-// state psi, the seven stage derivatives K_0..K_6 and the candidate ynew -- in
-// registers for the trajectory's whole life.  The only data that crosses lanes is
-// the stage vector entering each product M y: the lanes write their rows into a
-// small shared-memory exchange buffer (two alternating halves, one warp-level
-// barrier per product) and read back the entries their CSR rows need.  All
-// operators (M = -i H_eff, the C_n and the A_k) are staged once per CTA into
-// shared memory.  Groups pull trajectory ids from a global counter and start the
-// next trajectory as soon as theirs ends, so uneven trajectory lifetimes do not
-// idle lanes.  Every decision (accept/reject, crossing, output times, channel) is
-// taken from values reduced with a butterfly, which leaves the bitwise-identical
-// value in every lane of the group, so control flow is uniform per group.
+// gl owns rows gl, gl+G, ... (R of them) of every Dormand-Prince vector.  The
+// vectors of a trajectory -- the state psi, the candidate ynew, the seven stage
+// derivatives K_0..K_6 and a two-half exchange buffer -- live in the group's
+// slots of shared memory for the trajectory's whole life; nothing of the state
+// touches HBM.  A lane reads and writes only its own rows of psi, ynew and K;
+// the only data that crosses lanes is the vector entering each product M y,
+// which goes through the exchange buffer (one warp-level barrier per product).
+// All operators (M = -i H_eff, the C_n and the A_k) and the method's coefficient
+// tables are staged once per CTA into shared memory.  Keeping the vectors in
+// shared memory (not registers) lets the stage loops stay rolled, so the hot
+// loop fits the instruction cache, and leaves registers for more resident warps.
+// Groups pull trajectory ids from a global counter and start the next
+// trajectory as soon as theirs ends, so uneven lifetimes do not idle lanes.
+// Every decision (accept/reject, crossing, output times, channel) is taken from
+// values reduced with a butterfly, which leaves the bitwise-identical value in
+// every lane of the group, so control flow is uniform per group.
+//
+// The vector arithmetic is a policy (qtm_arith.cuh): complex128, double-float
+// (FP64-class precision on the FP32 pipe) or complex64.  Time, step size, the
+// crossing test and the jump-time root find are FP64 scalars in every policy.
 //
 // Per trajectory (paper step names):
 //   (A) r_0, c_0 from Philox(seed, traj, k = 0); output 0 = psi0;
@@ -30,141 +38,158 @@
 //       of the accepted step.
 #pragma once
 
+#include "qtm_arith.cuh"
 #include "qtm_device.cuh"
 #include "qtm_launch.h"
 
 namespace qtm {
 
-template <class V>
+// Vector slots of one trajectory group (each slot holds G * R complex rows).
+enum Slot { kPsi = 0, kYn = 1, kK0 = 2 /* K_q in kK0 + q, q = 0..6 */, kX0 = 9, kNumSlots = 11 };
+
+// Method coefficients in the policy's arithmetic, staged per CTA.
+template <class Ar>
+struct Coefs {
+    typename Ar::coef a[7][6];  // stage coupling a_sq (row 6 = 5th-order weights)
+    typename Ar::coef e[7];     // error weights b_q - bhat_q
+    typename Ar::coef W[7][5];  // continuous extension: coefficient of theta^(m+1) in w_j
+};
+
+template <class C>
 struct CsrView {
     const int *rp;
     const int *ci;
-    const cpx<V> *val;
+    const C *val;
 };
 
-template <class V>
-__device__ __forceinline__ CsrView<V> csr_view(const OpOffsets &o, const int *si, const cpx<V> *sv)
+template <class C>
+__device__ __forceinline__ CsrView<C> csr_view(const OpOffsets &o, const int *si, const C *sv)
 {
-    return CsrView<V>{si + o.rp, si + o.ci, sv + o.val};
+    return CsrView<C>{si + o.rp, si + o.ci, sv + o.val};
 }
 
-// Two alternating halves of the group's exchange buffer.  Each write is followed
-// by a group barrier before any lane reads, so a half is never rewritten while a
-// lane may still read it (that lane has passed the barrier of the write in between).
-template <class V>
-struct XBuf {
-    cpx<V> *base;
-    int np;
-    int cur;
-    __device__ __forceinline__ cpx<V> *next()
+// The group's shared-memory view: slots plus the current exchange half.
+template <class Ar, int G, int R>
+struct Lanes {
+    using cplx = typename Ar::cplx;
+    static constexpr int NP = G * R;
+    cplx *v;
+    int gl, n, x;
+    __device__ __forceinline__ cplx *slot(int s) const { return v + s * NP; }
+    __device__ __forceinline__ cplx *kq(int q) const { return v + (kK0 + q) * NP; }
+    // next half of the exchange buffer; every write to it is followed by a group
+    // barrier before any lane reads, so a half is never rewritten while a lane
+    // may still read it (that lane has passed the barrier of the write in between)
+    __device__ __forceinline__ cplx *xnext()
     {
-        cur ^= 1;
-        return base + cur * np;
+        x ^= 1;
+        return v + (kX0 + x) * NP;
     }
 };
 
-template <class V, int G, int R>
-__device__ __forceinline__ void put_rows(cpx<V> *buf, const cpx<V> (&y)[R], int gl, int n)
+// out[row] = (A x)[row] on the lane's rows
+template <class Ar, int G, int R>
+__device__ __forceinline__ void spmv_rows(const CsrView<typename Ar::cplx> &A, const typename Ar::cplx *x,
+                                          typename Ar::cplx *out, int gl, int n)
 {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int row = gl + G * r;
-        if (row < n) buf[row] = y[r];
-    }
-}
-
-// out = A buf on the lane's rows
-template <class V, int G, int R>
-__device__ __forceinline__ void spmv_rows(const CsrView<V> &A, const cpx<V> *buf, cpx<V> (&out)[R],
-                                          int gl, int n)
-{
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int row = gl + G * r;
-        cpx<V> acc = czero<V>();
         if (row < n) {
+            typename Ar::acc acc = Ar::zero();
             const int k1 = A.rp[row + 1];
-            for (int k = A.rp[row]; k < k1; ++k) acc = cmac(acc, A.val[k], buf[A.ci[k]]);
+            for (int k = A.rp[row]; k < k1; ++k) Ar::mac(acc, A.val[k], x[A.ci[k]]);
+            out[row] = Ar::get(acc);
         }
-        out[r] = acc;
     }
 }
 
-// y(t + theta h) = psi + h sum_j w_j(theta) K_j with w_j in monomial form
-template <class V, int R>
-__device__ __forceinline__ void dense_output(const cpx<V> (&psi)[R], const cpx<V> (&K)[7][R],
-                                             double h, double th, cpx<V> (&y)[R])
+// dst = psi + h sum_j w_j K_j on the lane's rows (the continuous extension at theta)
+template <class Ar, int G, int R>
+__device__ __forceinline__ void dense_rows(const Coefs<Ar> &C, const Lanes<Ar, G, R> &L, double h, double th,
+                                           typename Ar::cplx *dst)
 {
-    double w[7];
-#pragma unroll
-    for (int j = 0; j < 7; ++j) {
-        const double p = (((DP5::W(j, 5) * th + DP5::W(j, 4)) * th + DP5::W(j, 3)) * th
-                          + DP5::W(j, 2)) * th + DP5::W(j, 1);
-        w[j] = h * p * th;
-    }
+    typename Ar::coef w[7];
+    Ar::weights(th, &C.W[0][0], w);
+    const typename Ar::coef hc = Ar::coef_of(h);
+    const typename Ar::cplx *psi = L.slot(kPsi);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        cpx<V> acc = psi[r];
+        const int row = L.gl + G * r;
+        if (row < L.n) {
+            typename Ar::acc acc = Ar::zero();
 #pragma unroll
-        for (int j = 0; j < 7; ++j)
-            if (j != 1) acc = caxpy(acc, (V)w[j], K[j][r]);
-        y[r] = acc;
+            for (int j = 0; j < 7; ++j)
+                if (j != 1) Ar::axpy(acc, w[j], L.kq(j)[row]);
+            dst[row] = Ar::add_scaled(psi[row], hc, acc);
+        }
     }
 }
 
-// Output j: Re<y|A_k|y>/<y|y> for every observable, written by lane 0.
-template <class V, int G, int R>
-__device__ void record_outputs(const KernelArgs &a, const Group<G> &g, const int *si,
-                               const cpx<V> *sv, XBuf<V> &xb, const cpx<V> (&y)[R], int j,
-                               double *out)
+// Output j: Re<y|A_k|y>/<y|y> for every observable, written by lane 0.  y is in
+// the exchange half `y` and the group has synchronised after writing it.
+template <class Ar, int G, int R>
+__device__ __noinline__ void record_outputs(const KernelArgs &a, Group<G> g, const int *si,
+                                            const typename Ar::cplx *sv, const typename Ar::cplx *y, int j,
+                                            double *out)
 {
-    cpx<V> *b = xb.next();
-    put_rows<V, G, R>(b, y, g.gl, a.n);
-    g.sync();
-    double nn = 0.0;
+    using cplx = typename Ar::cplx;
+    typename Ar::red nn = Ar::rzero();
 #pragma unroll
-    for (int r = 0; r < R; ++r) nn += (double)cabs2(y[r]);
-    nn = g.sum(nn);
+    for (int r = 0; r < R; ++r) {
+        const int row = g.gl + G * r;
+        if (row < a.n) nn = Ar::radd(nn, Ar::abs2(y[row]));
+    }
+    nn = Ar::rsum(g, nn);
     for (int k = 0; k < a.n_obs; ++k) {
-        const CsrView<V> A = csr_view<V>(a.op[1 + a.n_c + k], si, sv);
-        cpx<V> ay[R];
-        spmv_rows<V, G, R>(A, b, ay, g.gl, a.n);
-        double ev = 0.0;
+        const CsrView<cplx> A = csr_view<cplx>(a.op[1 + a.n_c + k], si, sv);
+        typename Ar::red ev = Ar::rzero();
 #pragma unroll
-        for (int r = 0; r < R; ++r) ev += (double)y[r].re * ay[r].re + (double)y[r].im * ay[r].im;
-        ev = g.sum(ev);
-        if (g.gl == 0) out[(size_t)j * a.n_obs + k] = ev / nn;
+        for (int r = 0; r < R; ++r) {
+            const int row = g.gl + G * r;
+            if (row < a.n) {
+                typename Ar::acc acc = Ar::zero();
+                const int k1 = A.rp[row + 1];
+                for (int q = A.rp[row]; q < k1; ++q) Ar::mac(acc, A.val[q], y[A.ci[q]]);
+                ev = Ar::radd(ev, Ar::dot_re(y[row], Ar::get(acc)));
+            }
+        }
+        ev = Ar::rsum(g, ev);
+        if (g.gl == 0) out[(size_t)j * a.n_obs + k] = Ar::ratio(ev, nn);
     }
 }
 
 // First theta in (0, 1] where ||y(theta)||^2 = r.  ||y(theta)||^2 = sum_s P_s theta^s
 // with y(theta) = sum_m theta^m u_m, u_0 = psi, u_m = h sum_j W(j, m) K_j, and
 // P_s = sum_{m + m' = s} Re<u_m, u_m'>.
-template <class V, int G, int R>
-__device__ double locate_crossing(const Group<G> &g, const cpx<V> (&psi)[R],
-                                  const cpx<V> (&K)[7][R], double h, double r, int &iters)
+template <class Ar, int G, int R>
+__device__ __noinline__ double locate_crossing(const Coefs<Ar> &C, Lanes<Ar, G, R> L, Group<G> g, double h,
+                                               double r, int &iters)
 {
-    double gram[21];
+    using cplx = typename Ar::cplx;
+    typename Ar::red gram[21];
 #pragma unroll
-    for (int q = 0; q < 21; ++q) gram[q] = 0.0;
-#pragma unroll
+    for (int q = 0; q < 21; ++q) gram[q] = Ar::rzero();
+    const typename Ar::coef hc = Ar::coef_of(h);
+#pragma unroll 1
     for (int rr = 0; rr < R; ++rr) {
-        cpx<V> u[6];
-        u[0] = psi[rr];
+        const int row = L.gl + G * rr;
+        if (row >= L.n) continue;
+        cplx u[6];
+        u[0] = L.slot(kPsi)[row];
 #pragma unroll
         for (int m = 1; m <= 5; ++m) {
-            cpx<V> acc = czero<V>();
+            typename Ar::acc acc = Ar::zero();
 #pragma unroll
             for (int j = 0; j < 7; ++j)
-                if (DP5::W(j, m) != 0.0) acc = caxpy(acc, (V)(h * DP5::W(j, m)), K[j][rr]);
-            u[m] = acc;
+                if (j != 1) Ar::axpy(acc, C.W[j][m - 1], L.kq(j)[row]);
+            u[m] = Ar::add_scaled(Ar::czero(), hc, acc);
         }
         int q = 0;
 #pragma unroll
         for (int m = 0; m < 6; ++m)
 #pragma unroll
-            for (int m2 = m; m2 < 6; ++m2, ++q)
-                gram[q] += (double)u[m].re * u[m2].re + (double)u[m].im * u[m2].im;
+            for (int m2 = m; m2 < 6; ++m2, ++q) gram[q] = Ar::radd(gram[q], Ar::dot_re(u[m], u[m2]));
     }
     double P[11];
 #pragma unroll
@@ -175,7 +200,7 @@ __device__ double locate_crossing(const Group<G> &g, const cpx<V> (&psi)[R],
         for (int m = 0; m < 6; ++m)
 #pragma unroll
             for (int m2 = m; m2 < 6; ++m2, ++q) {
-                const double v = g.sum(gram[q]);
+                const double v = Ar::rval(Ar::rsum(g, gram[q]));
                 P[m + m2] += (m == m2) ? v : 2.0 * v;
             }
     }
@@ -223,78 +248,136 @@ __device__ double locate_crossing(const Group<G> &g, const cpx<V> (&psi)[R],
     return x;
 }
 
-template <class V, int G, int R>
-__device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int *si,
-                               const cpx<V> *sv, XBuf<V> &xb, long long il)
+// Step (C) after the crossing time is known: y = psi(tau) is in the exchange half
+// `y` (group synchronised).  Chooses the channel, writes C_n* y / ||C_n* y|| to
+// the psi slot, and returns the channel (or -1 when every weight is zero).
+template <class Ar, int G, int R>
+__device__ __noinline__ int apply_jump(const KernelArgs &a, Group<G> g, const int *si,
+                                       const typename Ar::cplx *sv, Lanes<Ar, G, R> L,
+                                       const typename Ar::cplx *y, double ck)
 {
+    using cplx = typename Ar::cplx;
+    double wq[kMaxChannels];
+    double wsum = 0.0;
+    cplx *tmp = L.slot(kYn);  // ynew is dead after a crossing
+    for (int q = 0; q < a.n_c; ++q) {
+        spmv_rows<Ar, G, R>(csr_view<cplx>(a.op[1 + q], si, sv), y, tmp, L.gl, L.n);
+        typename Ar::red part = Ar::rzero();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int row = L.gl + G * r;
+            if (row < L.n) part = Ar::radd(part, Ar::abs2(tmp[row]));
+        }
+        wq[q] = Ar::rval(Ar::rsum(g, part));
+        wsum += wq[q];
+    }
+    if (!(wsum > 0.0)) return -1;
+    const double target = ck * wsum;
+    double cum = 0.0;
+    int ch = a.n_c - 1;
+    for (int q = 0; q < a.n_c; ++q) {
+        cum += wq[q];
+        if (cum >= target) {
+            ch = q;
+            break;
+        }
+    }
+    cplx *psi = L.slot(kPsi);
+    spmv_rows<Ar, G, R>(csr_view<cplx>(a.op[1 + ch], si, sv), y, psi, L.gl, L.n);
+    const double nc = sqrt(wq[ch]);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int row = L.gl + G * r;
+        if (row < L.n) psi[row] = Ar::div(psi[row], nc);
+    }
+    return ch;
+}
+
+template <class Ar, int G, int R>
+__device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int *si,
+                               const typename Ar::cplx *sv, const Coefs<Ar> &C, Lanes<Ar, G, R> &L,
+                               long long il)
+{
+    using cplx = typename Ar::cplx;
     const int n = a.n;
     const int gl = g.gl;
     const long long traj = a.traj0 + il;
     const double t_end = a.t[a.n_t - 1];
     double *out = a.out + (size_t)il * a.n_t * a.n_obs;
-    const CsrView<V> M = csr_view<V>(a.op[0], si, sv);
+    const CsrView<cplx> M = csr_view<cplx>(a.op[0], si, sv);
     const double rtol = a.rtol, atol = a.atol;
+    cplx *psi = L.slot(kPsi);
+    cplx *yn = L.slot(kYn);
 
-    cpx<V> psi[R], K[7][R];
     int status = 0;
     long long attempts = 0;
     unsigned long long n_acc = 0, n_rej = 0, n_rhs = 0, n_jump = 0;
     int root_iters = 0;
 
-    const cpx<V> *psi0 = static_cast<const cpx<V> *>(a.psi0);
+    // (A)
+    const cplx *psi0 = static_cast<const cplx *>(a.psi0);
+    cplx *b = L.xnext();
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int row = gl + G * r;
-        psi[r] = row < n ? psi0[row] : czero<V>();
+        if (row < n) psi[row] = b[row] = psi0[row];
     }
-
-    // (A)
+    g.sync();
     long long k = 0;
     double rk, ck;
     jump_draws(a.seed, traj, k, rk, ck);
     double t = a.t[0];
-    record_outputs<V, G, R>(a, g, si, sv, xb, psi, 0, out);
+    record_outputs<Ar, G, R>(a, g, si, sv, b, 0, out);
     int j = 1;
+    spmv_rows<Ar, G, R>(M, b, L.kq(0), gl, n);
+    ++n_rhs;
 
-    {
-        cpx<V> *b = xb.next();
-        put_rows<V, G, R>(b, psi, gl, n);
-        g.sync();
-        spmv_rows<V, G, R>(M, b, K[0], gl, n);
-        ++n_rhs;
-    }
-
-    // starting step (Hairer, Norsett & Wanner, Sec. II.4)
+    // starting step (Hairer, Norsett & Wanner, Sec. II.4), in FP64 scalars
     double h;
     {
         const double span = t_end - t;
         double d0 = 0.0, d1 = 0.0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const double ay = sqrt((double)cabs2(psi[r]));
-            const double sc = atol + rtol * ay;
-            d0 += (double)cabs2(psi[r]) / (sc * sc);
-            d1 += (double)cabs2(K[0][r]) / (sc * sc);
+            const int row = gl + G * r;
+            if (row < n) {
+                const double yr = Ar::re(psi[row]), yi = Ar::im(psi[row]);
+                const double fr = Ar::re(L.kq(0)[row]), fi = Ar::im(L.kq(0)[row]);
+                const double sc = atol + rtol * sqrt(yr * yr + yi * yi);
+                d0 += (yr * yr + yi * yi) / (sc * sc);
+                d1 += (fr * fr + fi * fi) / (sc * sc);
+            }
         }
         d0 = sqrt(g.sum(d0) / n);
         d1 = sqrt(g.sum(d1) / n);
         double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
         if (h0 > span) h0 = span;
-        cpx<V> y1[R], f1[R];
+        const typename Ar::coef h0c = Ar::coef_of(h0);
+        b = L.xnext();
 #pragma unroll
-        for (int r = 0; r < R; ++r) y1[r] = caxpy(psi[r], (V)h0, K[0][r]);
-        cpx<V> *b = xb.next();
-        put_rows<V, G, R>(b, y1, gl, n);
+        for (int r = 0; r < R; ++r) {
+            const int row = gl + G * r;
+            if (row < n) {
+                typename Ar::acc acc = Ar::zero();
+                Ar::axpy(acc, Ar::coef_of(1.0), L.kq(0)[row]);
+                b[row] = Ar::add_scaled(psi[row], h0c, acc);
+            }
+        }
         g.sync();
-        spmv_rows<V, G, R>(M, b, f1, gl, n);
+        cplx *f1 = L.kq(1);  // scratch: K_1 is recomputed by the first step
+        spmv_rows<Ar, G, R>(M, b, f1, gl, n);
         ++n_rhs;
         double d2 = 0.0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const double ay = sqrt((double)cabs2(psi[r]));
-            const double sc = atol + rtol * ay;
-            const double dre = (double)f1[r].re - K[0][r].re, dim = (double)f1[r].im - K[0][r].im;
-            d2 += (dre * dre + dim * dim) / (sc * sc);
+            const int row = gl + G * r;
+            if (row < n) {
+                const double yr = Ar::re(psi[row]), yi = Ar::im(psi[row]);
+                const double sc = atol + rtol * sqrt(yr * yr + yi * yi);
+                const double dre = Ar::re(f1[row]) - Ar::re(L.kq(0)[row]);
+                const double dim = Ar::im(f1[row]) - Ar::im(L.kq(0)[row]);
+                d2 += (dre * dre + dim * dim) / (sc * sc);
+            }
         }
         d2 = sqrt(g.sum(d2) / n) / h0;
         const double dm = d1 > d2 ? d1 : d2;
@@ -306,7 +389,14 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
     bool rejected_before = false;
     while (j < a.n_t) {
         if (t_end - t <= 4.0 * 2.220446049250313e-16 * fabs(t_end)) {
-            for (; j < a.n_t; ++j) record_outputs<V, G, R>(a, g, si, sv, xb, psi, j, out);
+            b = L.xnext();
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int row = gl + G * r;
+                if (row < n) b[row] = psi[row];
+            }
+            g.sync();
+            for (; j < a.n_t; ++j) record_outputs<Ar, G, R>(a, g, si, sv, b, j, out);
             break;
         }
         if (attempts >= a.max_steps) {
@@ -323,54 +413,50 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
             break;
         }
 
-        // (B): one Dormand-Prince attempt; K[6] = M ynew
-        cpx<V> yn[R];
-#pragma unroll
+        // (B): one Dormand-Prince attempt; K_6 = M ynew
+        const typename Ar::coef hc = Ar::coef_of(h);
+#pragma unroll 1
         for (int s = 1; s < 7; ++s) {
-            cpx<V> ys[R];
+            b = L.xnext();
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                cpx<V> acc = czero<V>();
-#pragma unroll
-                for (int q = 0; q < 6; ++q)
-                    if (q < s && DP5::a(s, q) != 0.0) acc = caxpy(acc, (V)DP5::a(s, q), K[q][r]);
-                ys[r] = caxpy(psi[r], (V)h, acc);
+                const int row = gl + G * r;
+                if (row < n) {
+                    typename Ar::acc acc = Ar::zero();
+                    for (int q = 0; q < s; ++q) Ar::axpy(acc, C.a[s][q], L.kq(q)[row]);
+                    const cplx y = Ar::add_scaled(psi[row], hc, acc);
+                    b[row] = y;
+                    if (s == 6) yn[row] = y;
+                }
             }
-            if (s == 6) {
-#pragma unroll
-                for (int r = 0; r < R; ++r) yn[r] = ys[r];
-            }
-            cpx<V> *b = xb.next();
-            put_rows<V, G, R>(b, ys, gl, n);
             g.sync();
-            spmv_rows<V, G, R>(M, b, K[s], gl, n);
+            spmv_rows<Ar, G, R>(M, b, L.kq(s), gl, n);
         }
         n_rhs += 6;
         ++attempts;
 
-        double esum = 0.0;
+        typename Ar::errt esum = 0;
+        typename Ar::red nr = Ar::rzero();
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            if (gl + G * r < n) {
-                cpx<V> e = czero<V>();
+            const int row = gl + G * r;
+            if (row < n) {
+                typename Ar::acc e = Ar::zero();
 #pragma unroll
                 for (int q = 0; q < 7; ++q)
-                    if (DP5::e(q) != 0.0) e = caxpy(e, (V)DP5::e(q), K[q][r]);
-                const double ere = h * (double)e.re, eim = h * (double)e.im;
-                const double ay = sqrt((double)cabs2(psi[r]));
-                const double an = sqrt((double)cabs2(yn[r]));
-                const double sc = atol + rtol * (ay > an ? ay : an);
-                esum += (ere * ere + eim * eim) / (sc * sc);
+                    if (q != 1) Ar::axpy(e, C.e[q], L.kq(q)[row]);
+                esum += Ar::err_term(e, h, psi[row], yn[row], rtol, atol);
+                nr = Ar::radd(nr, Ar::abs2(yn[row]));
             }
         }
-        const double err = sqrt(g.sum(esum) / n);
+        const double err = Ar::err_final(Ar::err_sum(g, esum), n);
 
         if (!(err <= 1.0)) {
             if (!isfinite(err)) {
                 status = 6;
                 break;
             }
-            double fac = kSafety * pow(err, -0.2);
+            double fac = Ar::controller(err);
             if (fac < kFacMin) fac = kFacMin;
             h *= fac;
             rejected_before = true;
@@ -379,60 +465,28 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
         }
         ++n_acc;
         const double t_new = last ? t_end : t + h;
-        double nn = 0.0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) nn += (double)cabs2(yn[r]);
-        nn = g.sum(nn);
+        const double nn = Ar::rval(Ar::rsum(g, nr));
 
         if (nn < rk) {
             // (C): the norm reached r inside this step
-            const double th = locate_crossing<V, G, R>(g, psi, K, h, rk, root_iters);
+            const double th = locate_crossing<Ar, G, R>(C, L, g, h, rk, root_iters);
             double tau = t + th * h;
             if (tau > t_new) tau = t_new;
             for (; j < a.n_t && a.t[j] <= tau; ++j) {
                 double thj = (a.t[j] - t) / h;
                 if (thj > 1.0) thj = 1.0;
-                cpx<V> yd[R];
-                dense_output<V, R>(psi, K, h, thj, yd);
-                record_outputs<V, G, R>(a, g, si, sv, xb, yd, j, out);
+                b = L.xnext();
+                dense_rows<Ar, G, R>(C, L, h, thj, b);
+                g.sync();
+                record_outputs<Ar, G, R>(a, g, si, sv, b, j, out);
             }
-            cpx<V> yd[R];
-            dense_output<V, R>(psi, K, h, th, yd);
-            cpx<V> *b = xb.next();
-            put_rows<V, G, R>(b, yd, gl, n);
+            b = L.xnext();
+            dense_rows<Ar, G, R>(C, L, h, th, b);
             g.sync();
-            double wq[kMaxChannels];
-            double wsum = 0.0;
-            for (int q = 0; q < a.n_c; ++q) {
-                cpx<V> cy[R];
-                spmv_rows<V, G, R>(csr_view<V>(a.op[1 + q], si, sv), b, cy, gl, n);
-                double part = 0.0;
-#pragma unroll
-                for (int r = 0; r < R; ++r) part += (double)cabs2(cy[r]);
-                wq[q] = g.sum(part);
-                wsum += wq[q];
-            }
-            if (!(wsum > 0.0)) {
+            const int ch = apply_jump<Ar, G, R>(a, g, si, sv, L, b, ck);
+            if (ch < 0) {
                 status = 7;
                 break;
-            }
-            const double target = ck * wsum;
-            double cum = 0.0;
-            int ch = a.n_c - 1;
-            for (int q = 0; q < a.n_c; ++q) {
-                cum += wq[q];
-                if (cum >= target) {
-                    ch = q;
-                    break;
-                }
-            }
-            cpx<V> cy[R];
-            spmv_rows<V, G, R>(csr_view<V>(a.op[1 + ch], si, sv), b, cy, gl, n);
-            const double nc = sqrt(wq[ch]);
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                psi[r].re = (V)((double)cy[r].re / nc);
-                psi[r].im = (V)((double)cy[r].im / nc);
             }
             if (gl == 0 && (long long)n_jump < a.max_jumps) {
                 a.jump_t[(size_t)il * a.max_jumps + n_jump] = tau;
@@ -444,10 +498,14 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
             ++k;
             jump_draws(a.seed, traj, k, rk, ck);
             t = tau;
-            b = xb.next();
-            put_rows<V, G, R>(b, psi, gl, n);
+            b = L.xnext();
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int row = gl + G * r;
+                if (row < n) b[row] = psi[row];
+            }
             g.sync();
-            spmv_rows<V, G, R>(M, b, K[0], gl, n);
+            spmv_rows<Ar, G, R>(M, b, L.kq(0), gl, n);
             ++n_rhs;
             rejected_before = false;
             continue;
@@ -456,11 +514,12 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
         for (; j < a.n_t && a.t[j] <= t_new; ++j) {
             double thj = (a.t[j] - t) / h;
             if (thj > 1.0) thj = 1.0;
-            cpx<V> yd[R];
-            dense_output<V, R>(psi, K, h, thj, yd);
-            record_outputs<V, G, R>(a, g, si, sv, xb, yd, j, out);
+            b = L.xnext();
+            dense_rows<Ar, G, R>(C, L, h, thj, b);
+            g.sync();
+            record_outputs<Ar, G, R>(a, g, si, sv, b, j, out);
         }
-        double fac = (err == 0.0) ? kFacMax : kSafety * pow(err, -0.2);
+        double fac = (err == 0.0) ? kFacMax : Ar::controller(err);
         if (fac > kFacMax) fac = kFacMax;
         if (fac < kFacMin) fac = kFacMin;
         if (rejected_before && fac > 1.0) fac = 1.0;
@@ -468,8 +527,11 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
         t = t_new;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            psi[r] = yn[r];
-            K[0][r] = K[6][r];
+            const int row = gl + G * r;
+            if (row < n) {
+                psi[row] = yn[row];
+                L.kq(0)[row] = L.kq(6)[row];
+            }
         }
         h *= fac;
     }
@@ -477,7 +539,8 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
     if (gl == 0) {
         if (status != 0) {
             for (; j < a.n_t; ++j)
-                for (int q = 0; q < a.n_obs; ++q) out[(size_t)j * a.n_obs + q] = __longlong_as_double(0x7ff8000000000000LL);
+                for (int q = 0; q < a.n_obs; ++q)
+                    out[(size_t)j * a.n_obs + q] = __longlong_as_double(0x7ff8000000000000LL);
             atomicCAS(a.first_error, 0, status);
             atomicAdd(&a.counters[kFailed], 1ULL);
         }
@@ -490,43 +553,56 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
     }
 }
 
-template <class V, int G, int R, int BLOCK>
+template <class Ar, int G, int R, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) mcwf_kernel(const __grid_constant__ KernelArgs a)
 {
+    using cplx = typename Ar::cplx;
     extern __shared__ __align__(16) unsigned char smem[];
     int *si = reinterpret_cast<int *>(smem);
-    cpx<V> *sv = reinterpret_cast<cpx<V> *>(smem + a.smem_vals_offset);
+    cplx *sv = reinterpret_cast<cplx *>(smem + a.smem_vals_offset);
+    Coefs<Ar> *C = reinterpret_cast<Coefs<Ar> *>(smem + a.smem_coef_offset);
     for (int i = threadIdx.x; i < a.n_ints; i += BLOCK) si[i] = a.ints[i];
-    const cpx<V> *gv = static_cast<const cpx<V> *>(a.vals);
+    const cplx *gv = static_cast<const cplx *>(a.vals);
     for (int i = threadIdx.x; i < a.n_vals; i += BLOCK) sv[i] = gv[i];
+    for (int i = threadIdx.x; i < 42 + 7 + 35; i += BLOCK) {
+        if (i < 42)
+            C->a[i / 6][i % 6] = Ar::coef_of(DP5::a(i / 6, i % 6));
+        else if (i < 49)
+            C->e[i - 42] = Ar::coef_of(DP5::e(i - 42));
+        else
+            C->W[(i - 49) / 5][(i - 49) % 5] = Ar::coef_of(DP5::W((i - 49) / 5, (i - 49) % 5 + 1));
+    }
     __syncthreads();
 
     const Group<G> g(threadIdx.x & 31);
-    XBuf<V> xb{reinterpret_cast<cpx<V> *>(smem + a.smem_ybuf_offset) + (threadIdx.x / G) * 2 * (G * R),
-               G * R, 0};
+    Lanes<Ar, G, R> L{reinterpret_cast<cplx *>(smem + a.smem_ybuf_offset) + (threadIdx.x / G) * kNumSlots * (G * R),
+                      g.gl, a.n, 0};
     for (;;) {
         unsigned long long i = 0;
         if (g.gl == 0) i = atomicAdd(a.queue, 1ULL);
         i = g.bcast0(i);
         if ((long long)i >= a.ntraj) break;
-        run_trajectory<V, G, R>(a, g, si, sv, xb, (long long)i);
+        run_trajectory<Ar, G, R>(a, g, si, sv, *C, L, (long long)i);
     }
 }
 
 // Shared-memory layout and occupancy-sized persistent launch of one instantiation.
-template <class V, int G, int R>
+template <class Ar, int G, int R>
 cudaError_t launch_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInfo *info)
 {
+    using cplx = typename Ar::cplx;
     constexpr int BLOCK = 128;
     KernelArgs a = a0;
     auto al16 = [](size_t x) { return (x + 15) & ~size_t(15); };
     const size_t ib = al16((size_t)a.n_ints * sizeof(int));
-    const size_t vb = al16((size_t)a.n_vals * sizeof(cpx<V>));
+    const size_t vb = al16((size_t)a.n_vals * sizeof(cplx));
+    const size_t cb = al16(sizeof(Coefs<Ar>));
     a.smem_vals_offset = (int)ib;
-    a.smem_ybuf_offset = (int)(ib + vb);
-    const size_t smem = ib + vb + (size_t)(BLOCK / G) * 2 * G * R * sizeof(cpx<V>);
+    a.smem_coef_offset = (int)(ib + vb);
+    a.smem_ybuf_offset = (int)(ib + vb + cb);
+    const size_t smem = ib + vb + cb + (size_t)(BLOCK / G) * kNumSlots * G * R * sizeof(cplx);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    auto kern = mcwf_kernel<V, G, R, BLOCK>;
+    auto kern = mcwf_kernel<Ar, G, R, BLOCK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, nb = 0;
@@ -547,6 +623,18 @@ cudaError_t launch_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInf
         info->smem = smem;
     }
     return cudaGetLastError();
+}
+
+// Lanes per trajectory G and rows per lane R for dimension n (N <= G * R).
+template <class Ar>
+cudaError_t launch_for_dim(const KernelArgs &a, cudaStream_t stream, LaunchInfo *info)
+{
+    if (a.n <= 2) return launch_instance<Ar, 1, 2>(a, stream, info);
+    if (a.n <= 8) return launch_instance<Ar, 4, 2>(a, stream, info);
+    if (a.n <= 16) return launch_instance<Ar, 8, 2>(a, stream, info);
+    if (a.n <= 32) return launch_instance<Ar, 16, 2>(a, stream, info);
+    if (a.n <= 64) return launch_instance<Ar, 32, 2>(a, stream, info);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace qtm

@@ -247,6 +247,40 @@ void pack(qtm_ctx *ctx, const Csr &a)
     ctx->ops.push_back(o);
 }
 
+// Complex values in the layout of the kernel's arithmetic: (re, im) doubles for
+// complex128; (re_hi, re_lo, im_hi, im_lo) floats for double-float, with
+// hi = fl32(x) and lo = fl32(x - hi); (re, im) floats for complex64.
+std::vector<unsigned char> encode_values(const std::vector<cd> &v, int precision)
+{
+    std::vector<unsigned char> out;
+    if (precision == QTM_PREC_C128) {
+        out.resize(v.size() * sizeof(cd));
+        std::memcpy(out.data(), v.data(), out.size());
+    } else if (precision == QTM_PREC_DF64) {
+        std::vector<float> f(v.size() * 4);
+        for (size_t i = 0; i < v.size(); ++i) {
+            const double re = v[i].real(), im = v[i].imag();
+            const float rh = (float)re, ih = (float)im;
+            f[4 * i + 0] = rh;
+            f[4 * i + 1] = (float)(re - (double)rh);
+            f[4 * i + 2] = ih;
+            f[4 * i + 3] = (float)(im - (double)ih);
+        }
+        out.resize(f.size() * sizeof(float));
+        std::memcpy(out.data(), f.data(), out.size());
+    } else {
+        std::vector<float> f(v.size() * 2);
+        for (size_t i = 0; i < v.size(); ++i) {
+            f[2 * i] = (float)v[i].real();
+            f[2 * i + 1] = (float)v[i].imag();
+        }
+        out.resize(f.size() * sizeof(float));
+        std::memcpy(out.data(), f.data(), out.size());
+    }
+    if (out.empty()) out.resize(16);
+    return out;
+}
+
 void destroy_ctx(qtm_ctx *ctx)
 {
     if (!ctx) return;
@@ -325,7 +359,7 @@ qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
     if (!(p->rtol > 0.0) || !(p->atol >= 0.0) || !is_finite(p->rtol) || !is_finite(p->atol))
         return fail(nullptr, QTM_ERR_ARG, "qtm_create: need rtol > 0 and atol >= 0");
     if (p->max_steps <= 0) return fail(nullptr, QTM_ERR_ARG, "qtm_create: max_steps must be > 0");
-    if (p->precision != QTM_PREC_C128)
+    if (p->precision != QTM_PREC_C128 && p->precision != QTM_PREC_C64 && p->precision != QTM_PREC_DF64)
         return fail(nullptr, QTM_ERR_ARG, "qtm_create: unknown precision");
     if ((p->flags & ~QTM_FLAG_RECORD_JUMPS) != 0) return fail(nullptr, QTM_ERR_ARG, "qtm_create: unknown flags");
     if ((p->flags & QTM_FLAG_RECORD_JUMPS) && p->max_jumps_recorded < 1)
@@ -398,12 +432,15 @@ qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
         delete ctx;
         return s;
     }
-    const size_t ib = ctx->ints.size() * sizeof(int), vb = ctx->vals.size() * sizeof(cd);
+    // device representation of the complex values for the chosen arithmetic
+    std::vector<unsigned char> vals_dev = encode_values(ctx->vals, ctx->precision);
+    std::vector<unsigned char> psi0_dev = encode_values(ctx->psi0, ctx->precision);
+    const size_t ib = ctx->ints.size() * sizeof(int), vb = vals_dev.size();
     struct {
         DevBuf *b;
         size_t bytes;
     } allocs[] = {{&ctx->d_ints, ib}, {&ctx->d_vals, vb}, {&ctx->d_t, ctx->t.size() * sizeof(double)},
-                  {&ctx->d_psi0, (size_t)n * sizeof(cd)}, {&ctx->d_queue, 16},
+                  {&ctx->d_psi0, psi0_dev.size()}, {&ctx->d_queue, 16},
                   {&ctx->d_counters, qtm::kNumCounters * sizeof(unsigned long long)},
                   {&ctx->d_first_error, 16}};
     for (cudaEvent_t &ev : ctx->ev)
@@ -420,11 +457,11 @@ qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
         }
     }
     if ((e = cudaMemcpyAsync(ctx->d_ints.p, ctx->ints.data(), ib, cudaMemcpyHostToDevice, ctx->stream)) ||
-        (e = cudaMemcpyAsync(ctx->d_vals.p, ctx->vals.data(), vb, cudaMemcpyHostToDevice, ctx->stream)) ||
+        (e = cudaMemcpyAsync(ctx->d_vals.p, vals_dev.data(), vb, cudaMemcpyHostToDevice, ctx->stream)) ||
         (e = cudaMemcpyAsync(ctx->d_t.p, ctx->t.data(), ctx->t.size() * sizeof(double),
                              cudaMemcpyHostToDevice, ctx->stream)) ||
-        (e = cudaMemcpyAsync(ctx->d_psi0.p, ctx->psi0.data(), (size_t)n * sizeof(cd),
-                             cudaMemcpyHostToDevice, ctx->stream)) ||
+        (e = cudaMemcpyAsync(ctx->d_psi0.p, psi0_dev.data(), psi0_dev.size(), cudaMemcpyHostToDevice,
+                             ctx->stream)) ||
         (e = cudaStreamSynchronize(ctx->stream))) {
         qtm_status s = cuda_fail(nullptr, e, "qtm_create: upload");
         destroy_ctx(ctx);
@@ -494,7 +531,12 @@ qtm_status qtm_run_range(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64_t se
         a.n_jumps = (int *)ctx->d_njumps.p;
         a.jump_t = (double *)ctx->d_jump_t.p;
         a.jump_ch = (int *)ctx->d_jump_ch.p;
-        e = qtm::launch_mcwf_c128(a, ctx->stream, &ctx->info);
+        if (ctx->precision == QTM_PREC_DF64)
+            e = qtm::launch_mcwf_df64(a, ctx->stream, &ctx->info);
+        else if (ctx->precision == QTM_PREC_C64)
+            e = qtm::launch_mcwf_c64(a, ctx->stream, &ctx->info);
+        else
+            e = qtm::launch_mcwf_c128(a, ctx->stream, &ctx->info);
         if (e == cudaErrorInvalidValue)
             return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_run: no trajectory kernel fits this problem");
         if (e != cudaSuccess) return cuda_fail(ctx, e, "qtm_run: trajectory kernel launch");

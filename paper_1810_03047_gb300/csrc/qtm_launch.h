@@ -39,7 +39,8 @@ struct KernelArgs {
     double *jump_t;           // [ntraj][max_jumps]
     int *jump_ch;             // [ntraj][max_jumps]
     int smem_vals_offset;     // byte offset of the value array in dynamic shared memory
-    int smem_ybuf_offset;     // byte offset of the per-trajectory exchange buffers
+    int smem_coef_offset;     // byte offset of the method's coefficient tables
+    int smem_ybuf_offset;     // byte offset of the per-trajectory vector slots
 };
 
 enum CounterIndex { kAccepted = 0, kRejected, kRhs, kJumps, kRootIters, kFailed, kNumCounters };
@@ -56,6 +57,10 @@ constexpr int kMaxDimSparse = 64;
 // trajectory and rows per lane from args.n; returns cudaErrorInvalidValue when
 // no instantiation fits.
 cudaError_t launch_mcwf_c128(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+// Same kernel with double-float vectors (FP64-class precision on the FP32 pipe).
+cudaError_t launch_mcwf_df64(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+// Same kernel with complex64 vectors and double-float norms.
+cudaError_t launch_mcwf_c64(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
 
 // Ensemble reduction of out[ntraj][P] into sums, sums of squares, mean and
 // standard error, in a fixed summation order (bitwise reproducible).

@@ -32,6 +32,8 @@ QTM_ERR_UNSUPPORTED = 10
 QTM_FORMAT_DENSE = 0
 QTM_FORMAT_CSR = 1
 QTM_PREC_C128 = 0
+QTM_PREC_C64 = 1
+QTM_PREC_DF64 = 3
 QTM_FLAG_RECORD_JUMPS = 1
 
 # every entry point declared in include/qtm.h
