@@ -55,17 +55,18 @@ struct Coefs {
     typename Ar::coef W[7][5];  // continuous extension: coefficient of theta^(m+1) in w_j
 };
 
+// One operator in shared memory (SELL-G, see OpOffsets).
 template <class C>
 struct CsrView {
-    const int *rp;
-    const int *ci;
+    const int *tab;  // (off_r, width_r) pairs
+    const int *col;
     const C *val;
 };
 
 template <class C>
 __device__ __forceinline__ CsrView<C> csr_view(const OpOffsets &o, const int *si, const C *sv)
 {
-    return CsrView<C>{si + o.rp, si + o.ci, sv + o.val};
+    return CsrView<C>{si + o.table, si + o.cols, sv + o.vals};
 }
 
 // The group's shared-memory view: slots plus the current exchange half.
@@ -87,26 +88,34 @@ struct Lanes {
     }
 };
 
+// (A x)[row] for row = gl + G r (slice r of the SELL-G layout; the trip count is
+// uniform across the group, padded entries contribute 0 * x[0])
+template <class Ar, int G>
+__device__ __forceinline__ typename Ar::cplx spmv_row(const CsrView<typename Ar::cplx> &A,
+                                                      const typename Ar::cplx *x, int gl, int r)
+{
+    typename Ar::acc acc = Ar::zero();
+    const int off = A.tab[2 * r] + gl, w = A.tab[2 * r + 1];
+    for (int t = 0; t < w; ++t) Ar::mac(acc, A.val[off + t * G], x[A.col[off + t * G]]);
+    return Ar::get(acc);
+}
+
 // out[row] = (A x)[row] on the lane's rows
 template <class Ar, int G, int R>
 __device__ __forceinline__ void spmv_rows(const CsrView<typename Ar::cplx> &A, const typename Ar::cplx *x,
                                           typename Ar::cplx *out, int gl, int n)
 {
-#pragma unroll
+#pragma unroll 1
     for (int r = 0; r < R; ++r) {
+        const typename Ar::cplx v = spmv_row<Ar, G>(A, x, gl, r);
         const int row = gl + G * r;
-        if (row < n) {
-            typename Ar::acc acc = Ar::zero();
-            const int k1 = A.rp[row + 1];
-            for (int k = A.rp[row]; k < k1; ++k) Ar::mac(acc, A.val[k], x[A.ci[k]]);
-            out[row] = Ar::get(acc);
-        }
+        if (row < n) out[row] = v;
     }
 }
 
 // dst = psi + h sum_j w_j K_j on the lane's rows (the continuous extension at theta)
 template <class Ar, int G, int R>
-__device__ __forceinline__ void dense_rows(const Coefs<Ar> &C, const Lanes<Ar, G, R> &L, double h, double th,
+__device__ __noinline__ void dense_rows(const Coefs<Ar> &C, const Lanes<Ar, G, R> &L, double h, double th,
                                            typename Ar::cplx *dst)
 {
     typename Ar::coef w[7];
@@ -144,15 +153,11 @@ __device__ __noinline__ void record_outputs(const KernelArgs &a, Group<G> g, con
     for (int k = 0; k < a.n_obs; ++k) {
         const CsrView<cplx> A = csr_view<cplx>(a.op[1 + a.n_c + k], si, sv);
         typename Ar::red ev = Ar::rzero();
-#pragma unroll
+#pragma unroll 1
         for (int r = 0; r < R; ++r) {
+            const cplx ay = spmv_row<Ar, G>(A, y, g.gl, r);
             const int row = g.gl + G * r;
-            if (row < a.n) {
-                typename Ar::acc acc = Ar::zero();
-                const int k1 = A.rp[row + 1];
-                for (int q = A.rp[row]; q < k1; ++q) Ar::mac(acc, A.val[q], y[A.ci[q]]);
-                ev = Ar::radd(ev, Ar::dot_re(y[row], Ar::get(acc)));
-            }
+            if (row < a.n) ev = Ar::radd(ev, Ar::dot_re(y[row], ay));
         }
         ev = Ar::rsum(g, ev);
         if (g.gl == 0) out[(size_t)j * a.n_obs + k] = Ar::ratio(ev, nn);
@@ -418,7 +423,7 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
 #pragma unroll 1
         for (int s = 1; s < 7; ++s) {
             b = L.xnext();
-#pragma unroll
+#pragma unroll 1
             for (int r = 0; r < R; ++r) {
                 const int row = gl + G * r;
                 if (row < n) {
@@ -437,7 +442,7 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
 
         typename Ar::errt esum = 0;
         typename Ar::red nr = Ar::rzero();
-#pragma unroll
+#pragma unroll 1
         for (int r = 0; r < R; ++r) {
             const int row = gl + G * r;
             if (row < n) {
@@ -625,15 +630,15 @@ cudaError_t launch_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInf
     return cudaGetLastError();
 }
 
-// Lanes per trajectory G and rows per lane R for dimension n (N <= G * R).
+// The instantiation for the layout the operators were packed with (a.G, a.R).
 template <class Ar>
 cudaError_t launch_for_dim(const KernelArgs &a, cudaStream_t stream, LaunchInfo *info)
 {
-    if (a.n <= 2) return launch_instance<Ar, 1, 2>(a, stream, info);
-    if (a.n <= 8) return launch_instance<Ar, 4, 2>(a, stream, info);
-    if (a.n <= 16) return launch_instance<Ar, 8, 2>(a, stream, info);
-    if (a.n <= 32) return launch_instance<Ar, 16, 2>(a, stream, info);
-    if (a.n <= 64) return launch_instance<Ar, 32, 2>(a, stream, info);
+    if (a.G == 1 && a.R == 2) return launch_instance<Ar, 1, 2>(a, stream, info);
+    if (a.G == 4 && a.R == 2) return launch_instance<Ar, 4, 2>(a, stream, info);
+    if (a.G == 8 && a.R == 2) return launch_instance<Ar, 8, 2>(a, stream, info);
+    if (a.G == 16 && a.R == 2) return launch_instance<Ar, 16, 2>(a, stream, info);
+    if (a.G == 32 && a.R == 2) return launch_instance<Ar, 32, 2>(a, stream, info);
     return cudaErrorInvalidValue;
 }
 

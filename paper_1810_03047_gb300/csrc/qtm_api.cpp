@@ -65,6 +65,7 @@ struct qtm_ctx {
     std::vector<cd> psi0;
     DevBuf d_ints, d_vals, d_t, d_psi0, d_queue, d_counters, d_first_error;
     DevBuf d_out, d_partial, d_stats, d_njumps, d_jump_t, d_jump_ch;
+    qtm::Layout layout{0, 0};
     long long last_ntraj = -1;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // kernel start, kernel end, reduction end
     bool timed = false;
@@ -235,15 +236,33 @@ Csr effective_matrix(const Csr &H, const std::vector<Csr> &C)
     return M;
 }
 
-void pack(qtm_ctx *ctx, const Csr &a)
+// Appends operator a in SELL-G form (see OpOffsets) for the layout (G, R).
+void pack(qtm_ctx *ctx, const Csr &a, qtm::Layout lay)
 {
+    const int G = lay.G, R = lay.R, n = a.n;
     OpOffsets o;
-    o.rp = (int)ctx->ints.size();
-    ctx->ints.insert(ctx->ints.end(), a.rp.begin(), a.rp.end());
-    o.ci = (int)ctx->ints.size();
-    ctx->ints.insert(ctx->ints.end(), a.ci.begin(), a.ci.end());
-    o.val = (int)ctx->vals.size();
-    ctx->vals.insert(ctx->vals.end(), a.val.begin(), a.val.end());
+    o.table = (int)ctx->ints.size();
+    ctx->ints.resize(ctx->ints.size() + 2 * R, 0);
+    o.cols = (int)ctx->ints.size();
+    o.vals = (int)ctx->vals.size();
+    int off = 0;
+    for (int r = 0; r < R; ++r) {
+        int width = 0;
+        for (int gl = 0; gl < G; ++gl) {
+            const int row = gl + G * r;
+            if (row < n) width = std::max(width, a.rp[row + 1] - a.rp[row]);
+        }
+        ctx->ints[o.table + 2 * r] = off;
+        ctx->ints[o.table + 2 * r + 1] = width;
+        for (int t = 0; t < width; ++t)
+            for (int gl = 0; gl < G; ++gl) {
+                const int row = gl + G * r;
+                const bool has = row < n && t < a.rp[row + 1] - a.rp[row];
+                ctx->ints.push_back(has ? a.ci[a.rp[row] + t] : 0);
+                ctx->vals.push_back(has ? a.val[a.rp[row] + t] : cd(0.0));
+            }
+        off += width * G;
+    }
     ctx->ops.push_back(o);
 }
 
@@ -398,7 +417,7 @@ qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
         std::snprintf(buf, sizeof buf, "qtm_create: at most %d collapse operators", qtm::kMaxChannels);
         return fail(nullptr, QTM_ERR_UNSUPPORTED, buf);
     }
-    if (n > qtm::kMaxDimSparse) {
+    if (qtm::layout_for_dim(n).G == 0) {
         std::snprintf(buf, sizeof buf, "qtm_create: dim %d exceeds the largest supported dimension %d", n,
                       qtm::kMaxDimSparse);
         return fail(nullptr, QTM_ERR_UNSUPPORTED, buf);
@@ -422,9 +441,10 @@ qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
     const double nrm = std::sqrt(nn);
     ctx->psi0.resize(n);
     for (int i = 0; i < n; ++i) ctx->psi0[i] = cd(p->psi0[2 * i] / nrm, p->psi0[2 * i + 1] / nrm);
-    pack(ctx, effective_matrix(H, C));
-    for (const Csr &c : C) pack(ctx, c);
-    for (const Csr &a : A) pack(ctx, a);
+    ctx->layout = qtm::layout_for_dim(n);
+    pack(ctx, effective_matrix(H, C), ctx->layout);
+    for (const Csr &c : C) pack(ctx, c, ctx->layout);
+    for (const Csr &a : A) pack(ctx, a, ctx->layout);
 
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e != cudaSuccess) {
@@ -510,6 +530,8 @@ qtm_status qtm_run_range(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64_t se
         a.n_c = ctx->n_c;
         a.n_obs = ctx->n_obs;
         a.n_t = ctx->n_t;
+        a.G = ctx->layout.G;
+        a.R = ctx->layout.R;
         a.ints = (const int *)ctx->d_ints.p;
         a.vals = ctx->d_vals.p;
         a.n_ints = (int)ctx->ints.size();

@@ -10,15 +10,35 @@ namespace qtm {
 constexpr int kMaxOps = 64;        // M + collapse operators + observables
 constexpr int kMaxChannels = 48;   // collapse operators per problem
 
-// Offsets of one CSR operator inside the packed operator blob.
+// One operator inside the packed operator blob, stored as sliced ELLPACK with
+// slice height G (SELL-G): slice r holds rows gl + G r (gl = 0..G-1) and is
+// width_r entries wide; entry t of the row owned by lane gl sits at
+// off_r + t G + gl in both the column and the value array, so the lanes of a
+// group read consecutive words.  Short rows are padded with (column 0, value 0).
 struct OpOffsets {
-    int rp;   // row_ptr (n + 1 ints) in the int array
-    int ci;   // column indices in the int array
-    int val;  // values in the value array (complex elements)
+    int table;  // ints[table + 2 r] = off_r, ints[table + 2 r + 1] = width_r, r < R
+    int cols;   // column indices: ints[cols + off_r + t G + gl]
+    int vals;   // values: vals[vals + off_r + t G + gl] (complex elements)
 };
+
+// Lanes per trajectory G and state rows per lane R for dimension n (n <= G R);
+// G = 0 when no register-resident layout fits.
+struct Layout {
+    int G, R;
+};
+inline Layout layout_for_dim(int n)
+{
+    if (n <= 2) return Layout{1, 2};
+    if (n <= 8) return Layout{4, 2};
+    if (n <= 16) return Layout{8, 2};
+    if (n <= 32) return Layout{16, 2};
+    if (n <= 64) return Layout{32, 2};
+    return Layout{0, 0};
+}
 
 struct KernelArgs {
     int n, n_c, n_obs, n_t;
+    int G, R;                 // layout the operators were packed for
     // packed operators: op[0] = M = -i H_eff, op[1..n_c] = C_n, op[1+n_c..] = A_k
     const int *ints;
     const void *vals;         // cpx<V> elements of the kernel's value type
