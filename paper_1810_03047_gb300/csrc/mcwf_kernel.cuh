@@ -44,8 +44,11 @@
 
 namespace qtm {
 
-// Vector slots of one trajectory group (each slot holds G * R complex rows).
-enum Slot { kPsi = 0, kYn = 1, kK0 = 2 /* K_q in kK0 + q, q = 0..6 */, kX0 = 9, kNumSlots = 11 };
+// Vector slots of one trajectory group (each slot holds G * R complex rows).  The
+// candidate ynew shares K_1's slot: K_1 has zero weight in the 5th-order
+// solution, the error estimate and the continuous extension, so it is dead once
+// the last stage vector has been formed.
+enum Slot { kPsi = 0, kK0 = 1 /* K_q in kK0 + q, q = 0..6 */, kYn = 2 /* = K_1 */, kX0 = 8, kNumSlots = 10 };
 
 // Method coefficients in the policy's arithmetic, staged per CTA.
 template <class Ar>
@@ -55,18 +58,18 @@ struct Coefs {
     typename Ar::coef W[7][5];  // continuous extension: coefficient of theta^(m+1) in w_j
 };
 
-// One operator in shared memory (SELL-G, see OpOffsets).
-template <class C>
+// One operator in shared memory: its real and imaginary parts, each SELL-G (see OpOffsets).
+template <class Ar>
 struct CsrView {
-    const int *tab;  // (off_r, width_r) pairs
-    const int *col;
-    const C *val;
+    const int *tab_re, *col_re, *tab_im, *col_im;
+    const typename Ar::real *val_re, *val_im;
 };
 
-template <class C>
-__device__ __forceinline__ CsrView<C> csr_view(const OpOffsets &o, const int *si, const C *sv)
+template <class Ar>
+__device__ __forceinline__ CsrView<Ar> csr_view(const OpOffsets &o, const int *si, const typename Ar::real *sv)
 {
-    return CsrView<C>{si + o.table, si + o.cols, sv + o.vals};
+    return CsrView<Ar>{si + o.re.table, si + o.re.cols, si + o.im.table, si + o.im.cols,
+                       sv + o.re.vals, sv + o.im.vals};
 }
 
 // The group's shared-memory view: slots plus the current exchange half.
@@ -88,21 +91,26 @@ struct Lanes {
     }
 };
 
-// (A x)[row] for row = gl + G r (slice r of the SELL-G layout; the trip count is
+// (A x)[row] for row = gl + G r (slice r of the SELL-G parts; the trip counts are
 // uniform across the group, padded entries contribute 0 * x[0])
 template <class Ar, int G>
-__device__ __forceinline__ typename Ar::cplx spmv_row(const CsrView<typename Ar::cplx> &A,
-                                                      const typename Ar::cplx *x, int gl, int r)
+__device__ __forceinline__ typename Ar::cplx spmv_row(const CsrView<Ar> &A, const typename Ar::cplx *x, int gl,
+                                                      int r)
 {
     typename Ar::acc acc = Ar::zero();
-    const int off = A.tab[2 * r] + gl, w = A.tab[2 * r + 1];
-    for (int t = 0; t < w; ++t) Ar::mac(acc, A.val[off + t * G], x[A.col[off + t * G]]);
+    int off = A.tab_re[2 * r] + gl, w = A.tab_re[2 * r + 1];
+#pragma unroll 1
+    for (int t = 0; t < w; ++t) Ar::mac_re(acc, A.val_re[off + t * G], x[A.col_re[off + t * G]]);
+    off = A.tab_im[2 * r] + gl;
+    w = A.tab_im[2 * r + 1];
+#pragma unroll 1
+    for (int t = 0; t < w; ++t) Ar::mac_im(acc, A.val_im[off + t * G], x[A.col_im[off + t * G]]);
     return Ar::get(acc);
 }
 
 // out[row] = (A x)[row] on the lane's rows
 template <class Ar, int G, int R>
-__device__ __forceinline__ void spmv_rows(const CsrView<typename Ar::cplx> &A, const typename Ar::cplx *x,
+__device__ __forceinline__ void spmv_rows(const CsrView<Ar> &A, const typename Ar::cplx *x,
                                           typename Ar::cplx *out, int gl, int n)
 {
 #pragma unroll 1
@@ -127,7 +135,7 @@ __device__ __noinline__ void dense_rows(const Coefs<Ar> &C, const Lanes<Ar, G, R
         const int row = L.gl + G * r;
         if (row < L.n) {
             typename Ar::acc acc = Ar::zero();
-#pragma unroll
+#pragma unroll 1
             for (int j = 0; j < 7; ++j)
                 if (j != 1) Ar::axpy(acc, w[j], L.kq(j)[row]);
             dst[row] = Ar::add_scaled(psi[row], hc, acc);
@@ -139,7 +147,7 @@ __device__ __noinline__ void dense_rows(const Coefs<Ar> &C, const Lanes<Ar, G, R
 // the exchange half `y` and the group has synchronised after writing it.
 template <class Ar, int G, int R>
 __device__ __noinline__ void record_outputs(const KernelArgs &a, Group<G> g, const int *si,
-                                            const typename Ar::cplx *sv, const typename Ar::cplx *y, int j,
+                                            const typename Ar::real *sv, const typename Ar::cplx *y, int j,
                                             double *out)
 {
     using cplx = typename Ar::cplx;
@@ -151,7 +159,7 @@ __device__ __noinline__ void record_outputs(const KernelArgs &a, Group<G> g, con
     }
     nn = Ar::rsum(g, nn);
     for (int k = 0; k < a.n_obs; ++k) {
-        const CsrView<cplx> A = csr_view<cplx>(a.op[1 + a.n_c + k], si, sv);
+        const CsrView<Ar> A = csr_view<Ar>(a.op[1 + a.n_c + k], si, sv);
         typename Ar::red ev = Ar::rzero();
 #pragma unroll 1
         for (int r = 0; r < R; ++r) {
@@ -258,15 +266,15 @@ __device__ __noinline__ double locate_crossing(const Coefs<Ar> &C, Lanes<Ar, G, 
 // the psi slot, and returns the channel (or -1 when every weight is zero).
 template <class Ar, int G, int R>
 __device__ __noinline__ int apply_jump(const KernelArgs &a, Group<G> g, const int *si,
-                                       const typename Ar::cplx *sv, Lanes<Ar, G, R> L,
+                                       const typename Ar::real *sv, Lanes<Ar, G, R> L,
                                        const typename Ar::cplx *y, double ck)
 {
     using cplx = typename Ar::cplx;
     double wq[kMaxChannels];
     double wsum = 0.0;
-    cplx *tmp = L.slot(kYn);  // ynew is dead after a crossing
+    cplx *tmp = L.slot(kYn);  // ynew (in K_1's slot) is dead after a crossing
     for (int q = 0; q < a.n_c; ++q) {
-        spmv_rows<Ar, G, R>(csr_view<cplx>(a.op[1 + q], si, sv), y, tmp, L.gl, L.n);
+        spmv_rows<Ar, G, R>(csr_view<Ar>(a.op[1 + q], si, sv), y, tmp, L.gl, L.n);
         typename Ar::red part = Ar::rzero();
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -288,7 +296,7 @@ __device__ __noinline__ int apply_jump(const KernelArgs &a, Group<G> g, const in
         }
     }
     cplx *psi = L.slot(kPsi);
-    spmv_rows<Ar, G, R>(csr_view<cplx>(a.op[1 + ch], si, sv), y, psi, L.gl, L.n);
+    spmv_rows<Ar, G, R>(csr_view<Ar>(a.op[1 + ch], si, sv), y, psi, L.gl, L.n);
     const double nc = sqrt(wq[ch]);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -300,7 +308,7 @@ __device__ __noinline__ int apply_jump(const KernelArgs &a, Group<G> g, const in
 
 template <class Ar, int G, int R>
 __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int *si,
-                               const typename Ar::cplx *sv, const Coefs<Ar> &C, Lanes<Ar, G, R> &L,
+                               const typename Ar::real *sv, const Coefs<Ar> &C, Lanes<Ar, G, R> &L,
                                long long il)
 {
     using cplx = typename Ar::cplx;
@@ -309,7 +317,7 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
     const long long traj = a.traj0 + il;
     const double t_end = a.t[a.n_t - 1];
     double *out = a.out + (size_t)il * a.n_t * a.n_obs;
-    const CsrView<cplx> M = csr_view<cplx>(a.op[0], si, sv);
+    const CsrView<Ar> M = csr_view<Ar>(a.op[0], si, sv);
     const double rtol = a.rtol, atol = a.atol;
     cplx *psi = L.slot(kPsi);
     cplx *yn = L.slot(kYn);
@@ -428,6 +436,7 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
                 const int row = gl + G * r;
                 if (row < n) {
                     typename Ar::acc acc = Ar::zero();
+#pragma unroll 1
                     for (int q = 0; q < s; ++q) Ar::axpy(acc, C.a[s][q], L.kq(q)[row]);
                     const cplx y = Ar::add_scaled(psi[row], hc, acc);
                     b[row] = y;
@@ -447,7 +456,7 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
             const int row = gl + G * r;
             if (row < n) {
                 typename Ar::acc e = Ar::zero();
-#pragma unroll
+#pragma unroll 1
                 for (int q = 0; q < 7; ++q)
                     if (q != 1) Ar::axpy(e, C.e[q], L.kq(q)[row]);
                 esum += Ar::err_term(e, h, psi[row], yn[row], rtol, atol);
@@ -559,15 +568,16 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
 }
 
 template <class Ar, int G, int R, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) mcwf_kernel(const __grid_constant__ KernelArgs a)
+__global__ void __launch_bounds__(BLOCK, 4) mcwf_kernel(const __grid_constant__ KernelArgs a)
 {
     using cplx = typename Ar::cplx;
     extern __shared__ __align__(16) unsigned char smem[];
     int *si = reinterpret_cast<int *>(smem);
-    cplx *sv = reinterpret_cast<cplx *>(smem + a.smem_vals_offset);
+    using real = typename Ar::real;
+    real *sv = reinterpret_cast<real *>(smem + a.smem_vals_offset);
     Coefs<Ar> *C = reinterpret_cast<Coefs<Ar> *>(smem + a.smem_coef_offset);
     for (int i = threadIdx.x; i < a.n_ints; i += BLOCK) si[i] = a.ints[i];
-    const cplx *gv = static_cast<const cplx *>(a.vals);
+    const real *gv = static_cast<const real *>(a.vals);
     for (int i = threadIdx.x; i < a.n_vals; i += BLOCK) sv[i] = gv[i];
     for (int i = threadIdx.x; i < 42 + 7 + 35; i += BLOCK) {
         if (i < 42)
@@ -600,7 +610,7 @@ cudaError_t launch_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInf
     KernelArgs a = a0;
     auto al16 = [](size_t x) { return (x + 15) & ~size_t(15); };
     const size_t ib = al16((size_t)a.n_ints * sizeof(int));
-    const size_t vb = al16((size_t)a.n_vals * sizeof(cplx));
+    const size_t vb = al16((size_t)a.n_vals * sizeof(typename Ar::real));
     const size_t cb = al16(sizeof(Coefs<Ar>));
     a.smem_vals_offset = (int)ib;
     a.smem_coef_offset = (int)(ib + vb);
@@ -609,6 +619,9 @@ cudaError_t launch_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInf
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     auto kern = mcwf_kernel<Ar, G, R, BLOCK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    // the trajectory state lives in shared memory: ask for the largest carveout
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, nb = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;

@@ -59,7 +59,7 @@ struct qtm_ctx {
     double rtol = 0, atol = 0;
     long long max_steps = 0;
     std::vector<int> ints;
-    std::vector<cd> vals;
+    std::vector<double> reals;
     std::vector<OpOffsets> ops;
     std::vector<double> t;
     std::vector<cd> psi0;
@@ -236,34 +236,76 @@ Csr effective_matrix(const Csr &H, const std::vector<Csr> &C)
     return M;
 }
 
-// Appends operator a in SELL-G form (see OpOffsets) for the layout (G, R).
-void pack(qtm_ctx *ctx, const Csr &a, qtm::Layout lay)
+// Appends one real part of an operator (selected entries of a) in SELL-G form.
+qtm::SellPart pack_part(qtm_ctx *ctx, const Csr &a, bool imag, qtm::Layout lay)
 {
     const int G = lay.G, R = lay.R, n = a.n;
-    OpOffsets o;
+    std::vector<std::vector<std::pair<int, double>>> rows(n);
+    for (int i = 0; i < n; ++i)
+        for (int k = a.rp[i]; k < a.rp[i + 1]; ++k) {
+            const double v = imag ? a.val[k].imag() : a.val[k].real();
+            if (v != 0.0) rows[i].emplace_back(a.ci[k], v);
+        }
+    qtm::SellPart o;
     o.table = (int)ctx->ints.size();
     ctx->ints.resize(ctx->ints.size() + 2 * R, 0);
     o.cols = (int)ctx->ints.size();
-    o.vals = (int)ctx->vals.size();
+    o.vals = (int)ctx->reals.size();
     int off = 0;
     for (int r = 0; r < R; ++r) {
         int width = 0;
         for (int gl = 0; gl < G; ++gl) {
             const int row = gl + G * r;
-            if (row < n) width = std::max(width, a.rp[row + 1] - a.rp[row]);
+            if (row < n) width = std::max(width, (int)rows[row].size());
         }
         ctx->ints[o.table + 2 * r] = off;
         ctx->ints[o.table + 2 * r + 1] = width;
         for (int t = 0; t < width; ++t)
             for (int gl = 0; gl < G; ++gl) {
                 const int row = gl + G * r;
-                const bool has = row < n && t < a.rp[row + 1] - a.rp[row];
-                ctx->ints.push_back(has ? a.ci[a.rp[row] + t] : 0);
-                ctx->vals.push_back(has ? a.val[a.rp[row] + t] : cd(0.0));
+                const bool has = row < n && t < (int)rows[row].size();
+                ctx->ints.push_back(has ? rows[row][t].first : 0);
+                ctx->reals.push_back(has ? rows[row][t].second : 0.0);
             }
         off += width * G;
     }
+    return o;
+}
+
+// Appends operator a (both parts) for the layout (G, R).
+void pack(qtm_ctx *ctx, const Csr &a, qtm::Layout lay)
+{
+    OpOffsets o;
+    o.re = pack_part(ctx, a, false, lay);
+    o.im = pack_part(ctx, a, true, lay);
     ctx->ops.push_back(o);
+}
+
+// Real values in the layout of the kernel's arithmetic: doubles for complex128,
+// (hi, lo) float pairs with hi = fl32(x), lo = fl32(x - hi) for double-float,
+// floats for complex64.
+std::vector<unsigned char> encode_reals(const std::vector<double> &v, int precision)
+{
+    std::vector<unsigned char> out;
+    if (precision == QTM_PREC_C128) {
+        out.resize(v.size() * sizeof(double));
+        std::memcpy(out.data(), v.data(), out.size());
+    } else if (precision == QTM_PREC_DF64) {
+        std::vector<float> f(v.size() * 2);
+        for (size_t i = 0; i < v.size(); ++i) {
+            const float h = (float)v[i];
+            f[2 * i] = h;
+            f[2 * i + 1] = (float)(v[i] - (double)h);
+        }
+        out.resize(f.size() * sizeof(float));
+        std::memcpy(out.data(), f.data(), out.size());
+    } else {
+        std::vector<float> f(v.begin(), v.end());
+        out.resize(f.size() * sizeof(float));
+        std::memcpy(out.data(), f.data(), out.size());
+    }
+    if (out.empty()) out.resize(16);
+    return out;
 }
 
 // Complex values in the layout of the kernel's arithmetic: (re, im) doubles for
@@ -453,7 +495,7 @@ qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
         return s;
     }
     // device representation of the complex values for the chosen arithmetic
-    std::vector<unsigned char> vals_dev = encode_values(ctx->vals, ctx->precision);
+    std::vector<unsigned char> vals_dev = encode_reals(ctx->reals, ctx->precision);
     std::vector<unsigned char> psi0_dev = encode_values(ctx->psi0, ctx->precision);
     const size_t ib = ctx->ints.size() * sizeof(int), vb = vals_dev.size();
     struct {
@@ -535,7 +577,7 @@ qtm_status qtm_run_range(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64_t se
         a.ints = (const int *)ctx->d_ints.p;
         a.vals = ctx->d_vals.p;
         a.n_ints = (int)ctx->ints.size();
-        a.n_vals = (int)ctx->vals.size();
+        a.n_vals = (int)ctx->reals.size();
         for (size_t i = 0; i < ctx->ops.size(); ++i) a.op[i] = ctx->ops[i];
         a.t = (const double *)ctx->d_t.p;
         a.psi0 = ctx->d_psi0.p;

@@ -149,6 +149,7 @@ __device__ __forceinline__ df group_sum_df(const Group<G> &g, df v)
 struct ArF64 {
     static constexpr int kId = 0;
     using cplx = cpx<double>;
+    using real = double;
     using coef = double;
     struct acc {
         double re, im;
@@ -170,6 +171,17 @@ struct ArF64 {
     {
         a.re = fma(s, x.re, a.re);
         a.im = fma(s, x.im, a.im);
+    }
+    // a += v x and a += i v x for a real matrix entry v
+    __device__ static void mac_re(acc &a, real v, cplx x)
+    {
+        a.re = fma(v, x.re, a.re);
+        a.im = fma(v, x.im, a.im);
+    }
+    __device__ static void mac_im(acc &a, real v, cplx x)
+    {
+        a.re = fma(-v, x.im, a.re);
+        a.im = fma(v, x.re, a.im);
     }
     __device__ static cplx get(const acc &a) { return cplx{a.re, a.im}; }
     // y + h * a
@@ -228,6 +240,7 @@ struct __align__(16) cdf {
 struct ArDF {
     static constexpr int kId = 1;
     using cplx = cdf;
+    using real = df;
     using coef = df;
     struct acc {
         dacc re, im;
@@ -249,6 +262,16 @@ struct ArDF {
     {
         dacc_add_prod(a.re, s, x.re);
         dacc_add_prod(a.im, s, x.im);
+    }
+    __device__ static void mac_re(acc &a, real v, cplx x)
+    {
+        dacc_add_prod(a.re, v, x.re);
+        dacc_add_prod(a.im, v, x.im);
+    }
+    __device__ static void mac_im(acc &a, real v, cplx x)
+    {
+        dacc_add_prod(a.re, df{-v.hi, -v.lo}, x.im);
+        dacc_add_prod(a.im, v, x.re);
     }
     __device__ static cplx get(const acc &a) { return cplx{dacc_get(a.re), dacc_get(a.im)}; }
     __device__ static cplx add_scaled(cplx y, coef h, const acc &a)
@@ -307,11 +330,11 @@ struct ArDF {
     __device__ static void weights(double th, const coef *W, coef (&w)[7])
     {
         const df t = df_from_double(th);
-#pragma unroll
+#pragma unroll 1
         for (int j = 0; j < 7; ++j) {
             const coef *c = W + 5 * j;
             df p = c[4];
-#pragma unroll
+#pragma unroll 1
             for (int m = 3; m >= 0; --m) p = df_add(df_mul(p, t), c[m]);
             w[j] = df_mul(p, t);
         }
@@ -325,6 +348,7 @@ struct ArDF {
 struct ArF32 {
     static constexpr int kId = 2;
     using cplx = cpx<float>;
+    using real = float;
     using coef = float;
     struct acc {
         float re, im;
@@ -346,6 +370,16 @@ struct ArF32 {
     {
         a.re = fmaf(s, x.re, a.re);
         a.im = fmaf(s, x.im, a.im);
+    }
+    __device__ static void mac_re(acc &a, real v, cplx x)
+    {
+        a.re = fmaf(v, x.re, a.re);
+        a.im = fmaf(v, x.im, a.im);
+    }
+    __device__ static void mac_im(acc &a, real v, cplx x)
+    {
+        a.re = fmaf(-v, x.im, a.re);
+        a.im = fmaf(v, x.re, a.im);
     }
     __device__ static cplx get(const acc &a) { return cplx{a.re, a.im}; }
     __device__ static cplx add_scaled(cplx y, coef h, const acc &a)

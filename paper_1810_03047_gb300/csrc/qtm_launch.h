@@ -10,15 +10,22 @@ namespace qtm {
 constexpr int kMaxOps = 64;        // M + collapse operators + observables
 constexpr int kMaxChannels = 48;   // collapse operators per problem
 
-// One operator inside the packed operator blob, stored as sliced ELLPACK with
-// slice height G (SELL-G): slice r holds rows gl + G r (gl = 0..G-1) and is
-// width_r entries wide; entry t of the row owned by lane gl sits at
-// off_r + t G + gl in both the column and the value array, so the lanes of a
-// group read consecutive words.  Short rows are padded with (column 0, value 0).
-struct OpOffsets {
+// One operator inside the packed operator blob.  Its real and imaginary parts are
+// stored as two separate real matrices (an entry whose imaginary or real part is
+// zero appears in one of them only -- the matrices of Hermitian Hamiltonians
+// with real coefficients, -iH, are purely imaginary off the diagonal, so this
+// halves the multiply-adds).  Each part is sliced ELLPACK with slice height G
+// (SELL-G): slice r holds rows gl + G r (gl = 0..G-1) and is width_r entries
+// wide; entry t of the row owned by lane gl sits at off_r + t G + gl in both the
+// column and the value array, so the lanes of a group read consecutive words.
+// Short rows are padded with (column 0, value 0).
+struct SellPart {
     int table;  // ints[table + 2 r] = off_r, ints[table + 2 r + 1] = width_r, r < R
     int cols;   // column indices: ints[cols + off_r + t G + gl]
-    int vals;   // values: vals[vals + off_r + t G + gl] (complex elements)
+    int vals;   // real values: vals[vals + off_r + t G + gl]
+};
+struct OpOffsets {
+    SellPart re, im;
 };
 
 // Lanes per trajectory G and state rows per lane R for dimension n (n <= G R);
@@ -41,7 +48,7 @@ struct KernelArgs {
     int G, R;                 // layout the operators were packed for
     // packed operators: op[0] = M = -i H_eff, op[1..n_c] = C_n, op[1+n_c..] = A_k
     const int *ints;
-    const void *vals;         // cpx<V> elements of the kernel's value type
+    const void *vals;         // real values in the kernel's arithmetic (double, float pair or float)
     int n_ints, n_vals;
     OpOffsets op[kMaxOps];
     const double *t;          // n_t output times
