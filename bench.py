@@ -7,8 +7,12 @@ the FP64 ensemble reduction, on inputs already resident in device memory.
 
 Default workload: the damped, driven Jaynes-Cummings model (cavity Fock cutoff
 30 x qubit, N = 60, two collapse operators, 401 output times over t in [0, 40],
-observables a^dag a and sigma_+ sigma_-), 20,000 trajectories per GPU, complex128
-arithmetic, rtol 1e-8 / atol 1e-10, Philox seed 1.  Under torchrun each rank runs
+observables a^dag a and sigma_+ sigma_-), 20,000 trajectories per GPU, rtol 1e-8 /
+atol 1e-10, Philox seed 1.  The same ensemble is timed in three arithmetics:
+complex128 (the plain FP64 GPU path, whose means are the reference), the
+double-float path (FP64-class precision on the FP32 pipe) and complex64; the
+headline `value` is the fastest path whose ensemble stays within 1e-5 of the
+complex128 means.  Under torchrun each rank runs
 its own 20,000 trajectory ids (weak scaling); the FP64 sums are combined with one
 all-reduce per step.
 
@@ -49,8 +53,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precision", default="c128", choices=["c128", "df64", "c64"],
-                    help="trajectory arithmetic: complex128, double-float or complex64")
+    ap.add_argument("--only", choices=["c128", "df64", "c64"], default=None,
+                    help="time one arithmetic only (profiling); no observable-error comparison")
     return ap.parse_args()
 
 
@@ -203,6 +207,24 @@ def run_reference(args):
     return 0
 
 
+# FP32 pipe: 152 SMs x 128 lanes at 2070 MHz issue 40.3e12 FP32 instructions/s.
+# A double-float multiply-add (TwoProd, two cross FMAs, TwoSum, two adds) takes 12
+# FP32 instructions for 2 FP64-class flops, so the emulated FP64 peak is 1/6 of
+# the FP32 instruction rate.
+FP32_LANES_PER_SM = 128
+DF_INSTR_PER_FLOP = 6
+
+
+def peaks():
+    fp64 = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    fp32_instr = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
+    return {"c128": (fp64, "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz (GB300 nominal 1.25 TFLOP/s)"),
+            "df64": (fp32_instr / DF_INSTR_PER_FLOP / 1e12,
+                     "FP64-class flops on the FP32 pipe: 152 SMs x 128 FP32 lanes x 2070 MHz = 40.3e12 "
+                     "instr/s, 12 instructions per double-float multiply-add (2 flop)"),
+            "c64": (2 * fp32_instr / 1e12, "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz")}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -228,68 +250,102 @@ def main():
     first = rank * ntraj
     stream = torch.cuda.current_stream()
     Q.use_torch_allocator()
-    prec = {"c128": Q.QTM_PREC_C128, "df64": Q.QTM_PREC_DF64, "c64": Q.QTM_PREC_C64}[args.precision]
-    ctx = Q.qtm_create(prob, stream=int(stream.cuda_stream), precision=prec)
     P = len(prob.t) * len(prob.A)
     sums = torch.zeros(2 * P, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+    F = flops_per_attempt(prob.dim, nnz_m)
+    pk = peaks()
+    codes = {"c128": Q.QTM_PREC_C128, "df64": Q.QTM_PREC_DF64, "c64": Q.QTM_PREC_C64}
 
-    def step():
-        Q.qtm_run_range(ctx, first, ntraj, prob.seed)
+    def timed(prec_name, steps, warmup):
+        """Times `steps` passes of the path (trajectory kernel + ensemble reduction,
+        plus the all-reduce of the sums across GPUs) with L2 flushed in between."""
+        ctx = Q.qtm_create(prob, stream=int(stream.cuda_stream), precision=codes[prec_name])
+
+        def step():
+            Q.qtm_run_range(ctx, first, ntraj, prob.seed)
+            if world > 1:
+                Q.qtm_sums_device(ctx, sums.data_ptr(), sums.data_ptr() + 8 * P)
+                dist.all_reduce(sums)
+
+        for _ in range(max(warmup, 0)):
+            step()
+        torch.cuda.synchronize()
+        if Q.qtm_stats(ctx)["failed"]:
+            raise RuntimeError(f"{prec_name}: warm-up run failed")
         if world > 1:
-            Q.qtm_sums_device(ctx, sums.data_ptr(), sums.data_ptr() + 8 * P)
-            dist.all_reduce(sums)
-
-    for _ in range(max(args.warmup, 0)):
-        step()
-    torch.cuda.synchronize()
-    st = Q.qtm_stats(ctx)
-    if st["failed"]:
-        raise RuntimeError(f"warm-up run failed: {st}")
+            dist.barrier()
+        torch.cuda.synchronize()
+        total_ms, kernel_ms, attempts, launches = 0.0, [], 0, 0
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+            st = Q.qtm_stats(ctx)
+            kernel_ms.append(st["kernel_ms"])
+            attempts += st["accepted"] + st["rejected"]
+            launches += 5  # trajectory kernel + four ensemble-reduction kernels
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        mean, se = Q.qtm_expect(ctx)
+        last = Q.qtm_stats(ctx)
+        Q.qtm_destroy(ctx)
+        kern = sum(kernel_ms) / len(kernel_ms)
+        achieved = F * (attempts / steps) / (kern / 1e3) / 1e12
+        peak, note = pk[prec_name]
+        return {"value": world * ntraj * steps / (total_ms / 1e3), "ms_per_step": total_ms / steps,
+                "kernel_ms": kern, "mean": mean, "stats": last, "launches": launches,
+                "attempts_per_traj": attempts / steps / ntraj,
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak, "traffic": None,
+                             "kernel": f"qtm::mcwf_kernel<{prec_name},{last['kernel_group']},{last['kernel_rows']}>",
+                             "peak_note": note, "kernel_ms": kern}}
 
     clocks = ClockSampler(local)
     clocks.start()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    total_ms = 0.0
-    kernel_ms = []
-    attempts = 0
-    launches = 0
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        step()
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-        s = Q.qtm_stats(ctx)
-        kernel_ms.append(s["kernel_ms"])
-        attempts += s["accepted"] + s["rejected"]
-        launches += 5  # trajectory kernel + four reduction kernels
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    if args.only:
+        only = timed(args.only, args.steps, args.warmup)
+        clk = clocks.stop()
+        line = {"metric": METRIC, "value": only["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": only["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": args.only, "data": "synthetic",
+                "config": {"workload": desc, "ntraj_per_gpu": ntraj, "precision": args.only,
+                           "l2": "flushed between steps (256 MB write)",
+                           "parallelism": f"trajectory shards, {world} GPU(s)"},
+                "observable_error": None, "roofline": only["roofline"], "gpu_launches": only["launches"],
+                "clocks": clk, "note": "single-arithmetic profiling run"}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    ref = timed("c128", max(1, min(args.steps, 3)), max(1, min(args.warmup, 3)))
+    fast = timed("df64", args.steps, args.warmup)
+    mixed = timed("c64", max(1, min(args.steps, 3)), max(1, min(args.warmup, 3)))
     clk = clocks.stop()
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    mean, se = Q.qtm_expect(ctx)
-    last = Q.qtm_stats(ctx)
+    err_df = float(np.abs(fast["mean"] - ref["mean"]).max())
+    err_c64 = float(np.abs(mixed["mean"] - ref["mean"]).max())
+    head, head_name, head_err = (fast, "df64", err_df) if err_df <= 1e-5 else (ref, "c128", 0.0)
 
     # end to end through the public API with host buffers: create (H2D of the
     # problem), run, expect (D2H of mean and standard error), destroy
     e2e_steps = max(1, min(args.steps, 3))
-    h2d = d2h = 0
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        c2 = Q.qtm_create(prob, stream=int(stream.cuda_stream), precision=prec)
+        c2 = Q.qtm_create(prob, stream=int(stream.cuda_stream), precision=codes[head_name])
         Q.qtm_run_range(c2, first, ntraj, prob.seed)
         Q.qtm_expect(c2)
         Q.qtm_destroy(c2)
@@ -303,39 +359,37 @@ def main():
            + prob.psi0.nbytes + prob.t.nbytes)
     d2h = 2 * P * 8 + 4
 
-    value = world * ntraj * args.steps / (total_ms / 1e3)
-    F = flops_per_attempt(prob.dim, nnz_m)
-    kern_avg_ms = sum(kernel_ms) / len(kernel_ms)
-    achieved = F * (attempts / args.steps) / (kern_avg_ms / 1e3) / 1e12
-    fp64_peak = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    def side(r, err):
+        return {"value": r["value"], "ms_per_step": r["ms_per_step"], "observable_error": err,
+                "steps_per_trajectory": r["attempts_per_traj"], "roofline_frac": r["roofline"]["frac"],
+                "kernel_ms": r["kernel_ms"]}
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": desc, "ntraj_per_gpu": ntraj, "precision": "c128",
-                   "l2": "flushed between steps (256 MB write); operators are L2/SMEM-resident by design",
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": head_name, "data": "synthetic",
+        "config": {"workload": desc, "ntraj_per_gpu": ntraj, "precision": head_name,
+                   "l2": "flushed between steps (256 MB write); operators are shared-memory/L2 resident by design",
                    "parallelism": f"trajectory shards, {world} GPU(s)"},
-        "observable_error": 0.0,
-        "observable_error_note": "the complex128 path is the plain FP64 GPU path itself",
-        "rhs_evals_per_s": world * last["rhs_evals"] / (total_ms / 1e3 / args.steps),
-        "steps_per_trajectory": attempts / args.steps / ntraj,
-        "jumps_per_trajectory": last["jumps"] / ntraj,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp64_peak, "traffic": None,
-                     "kernel": "qtm::mcwf_kernel<double,32,2>",
-                     "peak_note": "FP64 FMA pipe, 152 SMs x 2 FMA/clk x 2070 MHz (nominal 1.25 TFLOP/s)",
-                     "kernel_ms": kern_avg_ms},
+        "observable_error": head_err,
+        "observable_error_note": "max |mean - mean of the complex128 (plain FP64) GPU path| over all output "
+                                 "times and observables, same seed and trajectories",
+        "fp64_path": side(ref, 0.0),
+        "c64_path": dict(side(mixed, err_c64), qualifies=err_c64 <= 1e-5),
+        "speedup_vs_fp64_path": head["value"] / ref["value"],
+        "rhs_evals_per_s": world * head["stats"]["rhs_evals"] / (head["ms_per_step"] / 1e3),
+        "steps_per_trajectory": head["attempts_per_traj"],
+        "jumps_per_trajectory": head["stats"]["jumps"] / ntraj,
+        "roofline": head["roofline"],
         "e2e": {"value": world * ntraj * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": launches,
+        "gpu_launches": ref["launches"] + fast["launches"] + mixed["launches"],
         "clocks": clk,
     }
     if world == 1 and rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds, rank)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    Q.qtm_destroy(ctx)
     if world > 1:
         dist.destroy_process_group()
     return 0
