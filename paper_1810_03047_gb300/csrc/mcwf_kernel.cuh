@@ -567,18 +567,38 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
     }
 }
 
+// Threads per CTA for a group size: 4 warps for single-warp groups, 8 warps (one
+// to four groups) for multi-warp groups.
+template <int G>
+__host__ __device__ constexpr int block_for_group() { return G <= 32 ? 128 : 256; }
+
+// Operators are staged into shared memory for single-warp groups (small N); the
+// operators of multi-warp groups (N > 64) are read from global memory, where
+// they stay resident in L2 and the L1 read-only path.
+template <int G>
+__host__ __device__ constexpr bool ops_in_shared() { return G <= 32; }
+
 template <class Ar, int G, int R, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 4) mcwf_kernel(const __grid_constant__ KernelArgs a)
+__global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 1)) mcwf_kernel(const __grid_constant__ KernelArgs a)
 {
     using cplx = typename Ar::cplx;
-    extern __shared__ __align__(16) unsigned char smem[];
-    int *si = reinterpret_cast<int *>(smem);
     using real = typename Ar::real;
-    real *sv = reinterpret_cast<real *>(smem + a.smem_vals_offset);
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int *si;
+    const real *sv;
+    if constexpr (ops_in_shared<G>()) {
+        int *ints = reinterpret_cast<int *>(smem);
+        real *vals = reinterpret_cast<real *>(smem + a.smem_vals_offset);
+        for (int i = threadIdx.x; i < a.n_ints; i += BLOCK) ints[i] = a.ints[i];
+        const real *gv = static_cast<const real *>(a.vals);
+        for (int i = threadIdx.x; i < a.n_vals; i += BLOCK) vals[i] = gv[i];
+        si = ints;
+        sv = vals;
+    } else {
+        si = a.ints;
+        sv = static_cast<const real *>(a.vals);
+    }
     Coefs<Ar> *C = reinterpret_cast<Coefs<Ar> *>(smem + a.smem_coef_offset);
-    for (int i = threadIdx.x; i < a.n_ints; i += BLOCK) si[i] = a.ints[i];
-    const real *gv = static_cast<const real *>(a.vals);
-    for (int i = threadIdx.x; i < a.n_vals; i += BLOCK) sv[i] = gv[i];
     for (int i = threadIdx.x; i < 42 + 7 + 35; i += BLOCK) {
         if (i < 42)
             C->a[i / 6][i % 6] = Ar::coef_of(DP5::a(i / 6, i % 6));
@@ -589,7 +609,7 @@ __global__ void __launch_bounds__(BLOCK, 4) mcwf_kernel(const __grid_constant__ 
     }
     __syncthreads();
 
-    const Group<G> g(threadIdx.x & 31);
+    const Group<G> g(threadIdx.x, reinterpret_cast<unsigned long long *>(smem + a.smem_scratch_offset));
     Lanes<Ar, G, R> L{reinterpret_cast<cplx *>(smem + a.smem_ybuf_offset) + (threadIdx.x / G) * kNumSlots * (G * R),
                       g.gl, a.n, 0};
     for (;;) {
@@ -606,16 +626,19 @@ template <class Ar, int G, int R>
 cudaError_t launch_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInfo *info)
 {
     using cplx = typename Ar::cplx;
-    constexpr int BLOCK = 128;
+    constexpr int BLOCK = block_for_group<G>();
+    constexpr int GROUPS = BLOCK / G;
     KernelArgs a = a0;
     auto al16 = [](size_t x) { return (x + 15) & ~size_t(15); };
-    const size_t ib = al16((size_t)a.n_ints * sizeof(int));
-    const size_t vb = al16((size_t)a.n_vals * sizeof(typename Ar::real));
+    const size_t ib = ops_in_shared<G>() ? al16((size_t)a.n_ints * sizeof(int)) : 0;
+    const size_t vb = ops_in_shared<G>() ? al16((size_t)a.n_vals * sizeof(typename Ar::real)) : 0;
     const size_t cb = al16(sizeof(Coefs<Ar>));
+    const size_t sb = al16((size_t)GROUPS * (Group<G>::kWarps + 1) * 8);
     a.smem_vals_offset = (int)ib;
     a.smem_coef_offset = (int)(ib + vb);
-    a.smem_ybuf_offset = (int)(ib + vb + cb);
-    const size_t smem = ib + vb + cb + (size_t)(BLOCK / G) * kNumSlots * G * R * sizeof(cplx);
+    a.smem_scratch_offset = (int)(ib + vb + cb);
+    a.smem_ybuf_offset = (int)(ib + vb + cb + sb);
+    const size_t smem = ib + vb + cb + sb + (size_t)GROUPS * kNumSlots * G * R * sizeof(cplx);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     auto kern = mcwf_kernel<Ar, G, R, BLOCK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -628,8 +651,7 @@ cudaError_t launch_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInf
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, BLOCK, smem)) != cudaSuccess) return e;
     if (nb < 1) nb = 1;
-    const long long per_cta = BLOCK / G;
-    const long long need = (a.ntraj + per_cta - 1) / per_cta;
+    const long long need = (a.ntraj + GROUPS - 1) / GROUPS;
     long long grid = (long long)nb * sms;
     if (need < grid) grid = need < 1 ? 1 : need;
     kern<<<(unsigned)grid, BLOCK, smem, stream>>>(a);
@@ -643,7 +665,8 @@ cudaError_t launch_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInf
     return cudaGetLastError();
 }
 
-// The instantiation for the layout the operators were packed with (a.G, a.R).
+// The instantiation for the layout the operators were packed with (a.G, a.R);
+// the layouts are those of layout_for_dim.
 template <class Ar>
 cudaError_t launch_for_dim(const KernelArgs &a, cudaStream_t stream, LaunchInfo *info)
 {
@@ -652,6 +675,10 @@ cudaError_t launch_for_dim(const KernelArgs &a, cudaStream_t stream, LaunchInfo 
     if (a.G == 8 && a.R == 2) return launch_instance<Ar, 8, 2>(a, stream, info);
     if (a.G == 16 && a.R == 2) return launch_instance<Ar, 16, 2>(a, stream, info);
     if (a.G == 32 && a.R == 2) return launch_instance<Ar, 32, 2>(a, stream, info);
+    if (a.G == 64 && a.R == 2) return launch_instance<Ar, 64, 2>(a, stream, info);
+    if (a.G == 128 && a.R == 2) return launch_instance<Ar, 128, 2>(a, stream, info);
+    if (a.G == 256 && a.R == 2) return launch_instance<Ar, 256, 2>(a, stream, info);
+    if (a.G == 256 && a.R == 4) return launch_instance<Ar, 256, 4>(a, stream, info);
     return cudaErrorInvalidValue;
 }
 

@@ -124,22 +124,35 @@ __device__ __forceinline__ void dacc_add(dacc &a, df x)
 
 __device__ __forceinline__ df dacc_get(dacc a) { return df_renorm(a.s, a.c); }
 
-// Butterfly sum of double-float values: every lane ends with the same bits
+// Group sum of double-float values: every thread ends with the same bits
 // (TwoSum's exact error does not depend on operand order and the low parts are
-// combined symmetrically).
+// combined symmetrically; per-warp totals of a multi-warp group are added in
+// warp order).
 template <int G>
 __device__ __forceinline__ df group_sum_df(const Group<G> &g, df v)
 {
+    constexpr int W = Group<G>::kMulti ? 32 : G;
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-        const float oh = __shfl_xor_sync(g.mask, v.hi, o, G);
-        const float ol = __shfl_xor_sync(g.mask, v.lo, o, G);
+    for (int o = W / 2; o > 0; o >>= 1) {
+        const float oh = __shfl_xor_sync(g.mask, v.hi, o, W);
+        const float ol = __shfl_xor_sync(g.mask, v.lo, o, W);
         float s, e;
         two_sum(v.hi, oh, s, e);
         e += v.lo + ol;
         v = df_renorm(s, e);
     }
-    return v;
+    if constexpr (Group<G>::kMulti) {
+        df *s = reinterpret_cast<df *>(g.scr);
+        if ((g.gl & 31) == 0) s[g.gl >> 5] = v;
+        g.sync();
+        df t = s[0];
+#pragma unroll
+        for (int w = 1; w < Group<G>::kWarps; ++w) t = df_add(t, s[w]);
+        g.sync();
+        return t;
+    } else {
+        return v;
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -181,34 +181,81 @@ constexpr double kFacMax = 10.0;
 // lanes sharing one trajectory
 // ---------------------------------------------------------------------------
 
-// G consecutive lanes of a warp (G a power of two, 1..32) integrate one
-// trajectory; lane gl owns state rows gl, gl + G, gl + 2G, ...
+// G consecutive threads integrate one trajectory; thread gl of the group owns
+// state rows gl, gl + G, gl + 2G, ...  G is a power of two: 1..32 lanes of one
+// warp, or 64..256 threads spanning G/32 warps.  Within a warp the group
+// synchronises with __syncwarp and reduces with a butterfly of shuffles, which
+// leaves the bitwise-identical total in every lane.  A multi-warp group
+// synchronises with the named barrier (1 + its index in the CTA) and reduces
+// each warp by butterfly, then adds the per-warp totals through a small
+// shared-memory scratch in warp order -- again identical in every thread.
 template <int G>
 struct Group {
+    static constexpr bool kMulti = G > 32;
+    static constexpr int kWarps = kMulti ? G / 32 : 1;
     unsigned mask;
     int gl;
-    __device__ explicit Group(int lane)
+    int bar;                   // named barrier id (multi-warp groups)
+    unsigned long long *scr;   // kWarps + 1 eight-byte slots (multi-warp groups)
+
+    // tid: thread index in the CTA; scratch: the CTA's group scratch area
+    __device__ Group(int tid, unsigned long long *scratch)
     {
-        gl = lane & (G - 1);
-        mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+        if constexpr (kMulti) {
+            gl = tid & (G - 1);
+            mask = 0xffffffffu;
+            bar = 1 + tid / G;
+            scr = scratch + (size_t)(tid / G) * (kWarps + 1);
+        } else {
+            const int lane = tid & 31;
+            gl = lane & (G - 1);
+            mask = (G == 32) ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+            bar = 0;
+            scr = nullptr;
+        }
     }
     __device__ __forceinline__ void sync() const
     {
-        if (G > 1) __syncwarp(mask);
+        if constexpr (kMulti)
+            asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(G) : "memory");
+        else if (G > 1)
+            __syncwarp(mask);
     }
-    // butterfly sum: every lane ends with the bitwise-identical total
     template <class T>
     __device__ __forceinline__ T sum(T v) const
     {
+        constexpr int W = kMulti ? 32 : G;
 #pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, G);
-        return v;
+        for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o, W);
+        if constexpr (kMulti) {
+            static_assert(sizeof(T) <= 8, "scratch slots hold 8 bytes");
+            T *s = reinterpret_cast<T *>(scr);
+            if ((gl & 31) == 0) s[gl >> 5] = v;
+            sync();
+            T t = s[0];
+#pragma unroll
+            for (int w = 1; w < kWarps; ++w) t += s[w];
+            sync();
+            return t;
+        } else {
+            return v;
+        }
     }
     template <class T>
     __device__ __forceinline__ T bcast0(T v) const
     {
-        if (G == 1) return v;
-        return __shfl_sync(mask, v, 0, G);
+        if constexpr (kMulti) {
+            static_assert(sizeof(T) <= 8, "scratch slots hold 8 bytes");
+            T *s = reinterpret_cast<T *>(scr + kWarps);
+            if (gl == 0) *s = v;
+            sync();
+            const T t = *s;
+            sync();
+            return t;
+        } else {
+            if (G == 1) return v;
+            return __shfl_sync(mask, v, 0, G);
+        }
     }
 };
 

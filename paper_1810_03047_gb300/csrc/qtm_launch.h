@@ -40,6 +40,10 @@ inline Layout layout_for_dim(int n)
     if (n <= 16) return Layout{8, 2};
     if (n <= 32) return Layout{16, 2};
     if (n <= 64) return Layout{32, 2};
+    if (n <= 128) return Layout{64, 2};
+    if (n <= 256) return Layout{128, 2};
+    if (n <= 512) return Layout{256, 2};
+    if (n <= 1024) return Layout{256, 4};
     return Layout{0, 0};
 }
 
@@ -67,6 +71,7 @@ struct KernelArgs {
     int *jump_ch;             // [ntraj][max_jumps]
     int smem_vals_offset;     // byte offset of the value array in dynamic shared memory
     int smem_coef_offset;     // byte offset of the method's coefficient tables
+    int smem_scratch_offset;  // byte offset of the multi-warp groups' reduction scratch
     int smem_ybuf_offset;     // byte offset of the per-trajectory vector slots
 };
 
@@ -77,8 +82,9 @@ struct LaunchInfo {
     size_t smem;
 };
 
-// Largest dimension the register-resident trajectory kernels handle.
-constexpr int kMaxDimSparse = 64;
+// Largest dimension the trajectory kernels handle (ten state vectors of N complex
+// values per trajectory must fit in shared memory).
+constexpr int kMaxDimSparse = 1024;
 
 // FP64 (complex128) trajectory kernel, CSR operators.  Chooses lanes per
 // trajectory and rows per lane from args.n; returns cudaErrorInvalidValue when

@@ -91,7 +91,7 @@ def test_rejects_unknown_precision_and_flags():
 
 
 def test_too_large_dimension_is_unsupported():
-    prob = S.ising_chain(7)  # N = 128
+    prob = S.ising_chain(11)  # N = 2048: ten state vectors no longer fit in shared memory
     _expect_error(prob, Q.QTM_ERR_UNSUPPORTED, "dimension")
 
 
