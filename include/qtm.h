@@ -173,6 +173,30 @@ qtm_status qtm_run(qtm_ctx *ctx, int64_t ntraj, uint64_t seed);
  * a single larger run. */
 qtm_status qtm_run_range(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64_t seed);
 
+/* Runs several ensembles at once: context i runs its trajectories 0 .. ntraj[i]-1
+ * keyed by seed.  All runs are captured into one CUDA graph -- each system's
+ * persistent kernel and reduction on its own branch -- and launched on the
+ * stream of ctxs[0]; the other contexts' streams wait for that launch, so each
+ * context's results are read with qtm_expect as usual.  Systems of different
+ * dimension (e.g. Ising chains of several lengths) thus share the GPU in one
+ * submission, and the tail of one system overlaps the others.  All contexts must
+ * be on the same device and distinct.  qtm_stats of a batched run reports no
+ * kernel times (kernel_ms = 0). */
+qtm_status qtm_run_batch(qtm_ctx *const *ctxs, const int64_t *ntraj, int32_t n, uint64_t seed);
+
+/* Times the lane layouts available for the context's dimension (threads per
+ * trajectory x state rows per thread, see qtm_stats_t.kernel_group / kernel_rows)
+ * on a run of `sample` trajectories keyed by seed, keeps the fastest, and returns
+ * it in *group and *rows (either may be NULL).  Results of later runs do not
+ * depend on the layout beyond round-off.  Synchronises; discards the sample's
+ * results. */
+qtm_status qtm_autotune(qtm_ctx *ctx, int64_t sample, uint64_t seed, int32_t *group, int32_t *rows);
+
+/* Selects one of the lane layouts qtm_autotune would consider for the context's
+ * dimension (e.g. a layout found by an earlier qtm_autotune); QTM_ERR_UNSUPPORTED
+ * for any other pair.  Synchronises; discards the results of earlier runs. */
+qtm_status qtm_set_layout(qtm_ctx *ctx, int32_t group, int32_t rows);
+
 /* Ensemble mean (n_t * n_obs doubles, output-major: [j * n_obs + k]) and, if
  * stderr_out is not NULL, the standard error sqrt(var / n) with the sample
  * variance (n - 1 divisor; 0 when n < 2).  Synchronises; returns the first

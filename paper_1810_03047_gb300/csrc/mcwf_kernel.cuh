@@ -665,18 +665,31 @@ cudaError_t launch_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInf
     return cudaGetLastError();
 }
 
-// The instantiation for the layout the operators were packed with (a.G, a.R);
-// the layouts are those of layout_for_dim.
+// The instantiation for the layout the operators were packed with (a.G, a.R):
+// single-warp groups here, multi-warp groups in launch_large.  The layouts are
+// those of layout_candidates.
 template <class Ar>
-cudaError_t launch_for_dim(const KernelArgs &a, cudaStream_t stream, LaunchInfo *info)
+cudaError_t launch_small(const KernelArgs &a, cudaStream_t stream, LaunchInfo *info)
 {
     if (a.G == 1 && a.R == 2) return launch_instance<Ar, 1, 2>(a, stream, info);
     if (a.G == 4 && a.R == 2) return launch_instance<Ar, 4, 2>(a, stream, info);
+    if (a.G == 4 && a.R == 4) return launch_instance<Ar, 4, 4>(a, stream, info);
     if (a.G == 8 && a.R == 2) return launch_instance<Ar, 8, 2>(a, stream, info);
+    if (a.G == 8 && a.R == 4) return launch_instance<Ar, 8, 4>(a, stream, info);
     if (a.G == 16 && a.R == 2) return launch_instance<Ar, 16, 2>(a, stream, info);
+    if (a.G == 16 && a.R == 4) return launch_instance<Ar, 16, 4>(a, stream, info);
     if (a.G == 32 && a.R == 2) return launch_instance<Ar, 32, 2>(a, stream, info);
+    if (a.G == 32 && a.R == 4) return launch_instance<Ar, 32, 4>(a, stream, info);
+    return cudaErrorInvalidValue;
+}
+
+template <class Ar>
+cudaError_t launch_large(const KernelArgs &a, cudaStream_t stream, LaunchInfo *info)
+{
     if (a.G == 64 && a.R == 2) return launch_instance<Ar, 64, 2>(a, stream, info);
+    if (a.G == 64 && a.R == 4) return launch_instance<Ar, 64, 4>(a, stream, info);
     if (a.G == 128 && a.R == 2) return launch_instance<Ar, 128, 2>(a, stream, info);
+    if (a.G == 128 && a.R == 4) return launch_instance<Ar, 128, 4>(a, stream, info);
     if (a.G == 256 && a.R == 2) return launch_instance<Ar, 256, 2>(a, stream, info);
     if (a.G == 256 && a.R == 4) return launch_instance<Ar, 256, 4>(a, stream, info);
     return cudaErrorInvalidValue;

@@ -63,6 +63,8 @@ struct qtm_ctx {
     std::vector<OpOffsets> ops;
     std::vector<double> t;
     std::vector<cd> psi0;
+    Csr M;                       // host copies of the operators, for repacking
+    std::vector<Csr> Cops, Aops;
     DevBuf d_ints, d_vals, d_t, d_psi0, d_queue, d_counters, d_first_error;
     DevBuf d_out, d_partial, d_stats, d_njumps, d_jump_t, d_jump_ch;
     qtm::Layout layout{0, 0};
@@ -281,6 +283,18 @@ void pack(qtm_ctx *ctx, const Csr &a, qtm::Layout lay)
     ctx->ops.push_back(o);
 }
 
+// Packs every operator (M, the C_n, the A_k) for layout lay (host side only).
+void repack(qtm_ctx *ctx, qtm::Layout lay)
+{
+    ctx->layout = lay;
+    ctx->ints.clear();
+    ctx->reals.clear();
+    ctx->ops.clear();
+    pack(ctx, ctx->M, lay);
+    for (const Csr &c : ctx->Cops) pack(ctx, c, lay);
+    for (const Csr &a : ctx->Aops) pack(ctx, a, lay);
+}
+
 // Real values in the layout of the kernel's arithmetic: doubles for complex128,
 // (hi, lo) float pairs with hi = fl32(x), lo = fl32(x - hi) for double-float,
 // floats for complex64.
@@ -483,10 +497,10 @@ qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
     const double nrm = std::sqrt(nn);
     ctx->psi0.resize(n);
     for (int i = 0; i < n; ++i) ctx->psi0[i] = cd(p->psi0[2 * i] / nrm, p->psi0[2 * i + 1] / nrm);
-    ctx->layout = qtm::layout_for_dim(n);
-    pack(ctx, effective_matrix(H, C), ctx->layout);
-    for (const Csr &c : C) pack(ctx, c, ctx->layout);
-    for (const Csr &a : A) pack(ctx, a, ctx->layout);
+    ctx->M = effective_matrix(H, C);
+    ctx->Cops = C;
+    ctx->Aops = A;
+    repack(ctx, qtm::layout_for_dim(n));
 
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e != cudaSuccess) {
@@ -533,12 +547,9 @@ qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
     return QTM_OK;
 }
 
-qtm_status qtm_run_range(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64_t seed)
+// Device buffers of a run of ntraj trajectories (grown, never shrunk).
+static qtm_status reserve_run(qtm_ctx *ctx, int64_t ntraj)
 {
-    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_run: ctx is NULL");
-    ctx->err.clear();
-    if (first < 0 || ntraj < 0) return fail(ctx, QTM_ERR_ARG, "qtm_run: first and ntraj must be >= 0");
-    if (ntraj > ((int64_t)1 << 40)) return fail(ctx, QTM_ERR_ARG, "qtm_run: ntraj too large");
     const size_t P = (size_t)ctx->n_t * ctx->n_obs;
     const int S = qtm::reduce_segments(ntraj);
     cudaError_t e;
@@ -551,20 +562,29 @@ qtm_status qtm_run_range(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64_t se
             (e = dev_reserve(ctx, ctx->d_jump_t, (size_t)ntraj * ctx->max_jumps * sizeof(double))) ||
             (e = dev_reserve(ctx, ctx->d_jump_ch, (size_t)ntraj * ctx->max_jumps * sizeof(int))))
             return cuda_fail(ctx, e, "qtm_run: device allocation");
-        if ((e = cudaMemsetAsync(ctx->d_njumps.p, 0, (size_t)ntraj * sizeof(int), ctx->stream)) ||
-            (e = cudaMemsetAsync(ctx->d_jump_t.p, 0xff, (size_t)ntraj * ctx->max_jumps * sizeof(double),
-                                 ctx->stream)) ||
-            (e = cudaMemsetAsync(ctx->d_jump_ch.p, 0xff, (size_t)ntraj * ctx->max_jumps * sizeof(int),
-                                 ctx->stream)))
+    }
+    return QTM_OK;
+}
+
+// Enqueues one run on stream s (buffers reserved): counter resets, the
+// trajectory kernel and the ensemble reduction; with_events brackets them with
+// the context's timing events.  Performs no allocation, so it can be captured.
+static qtm_status enqueue_run(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64_t seed, cudaStream_t s,
+                              bool with_events)
+{
+    const size_t P = (size_t)ctx->n_t * ctx->n_obs;
+    cudaError_t e;
+    if (ctx->max_jumps > 0) {
+        if ((e = cudaMemsetAsync(ctx->d_njumps.p, 0, (size_t)ntraj * sizeof(int), s)) ||
+            (e = cudaMemsetAsync(ctx->d_jump_t.p, 0xff, (size_t)ntraj * ctx->max_jumps * sizeof(double), s)) ||
+            (e = cudaMemsetAsync(ctx->d_jump_ch.p, 0xff, (size_t)ntraj * ctx->max_jumps * sizeof(int), s)))
             return cuda_fail(ctx, e, "qtm_run: cudaMemsetAsync");
     }
-    if ((e = cudaMemsetAsync(ctx->d_queue.p, 0, 16, ctx->stream)) ||
-        (e = cudaMemsetAsync(ctx->d_counters.p, 0, qtm::kNumCounters * sizeof(unsigned long long),
-                             ctx->stream)) ||
-        (e = cudaMemsetAsync(ctx->d_first_error.p, 0, 16, ctx->stream)))
+    if ((e = cudaMemsetAsync(ctx->d_queue.p, 0, 16, s)) ||
+        (e = cudaMemsetAsync(ctx->d_counters.p, 0, qtm::kNumCounters * sizeof(unsigned long long), s)) ||
+        (e = cudaMemsetAsync(ctx->d_first_error.p, 0, 16, s)))
         return cuda_fail(ctx, e, "qtm_run: cudaMemsetAsync");
-
-    if ((e = cudaEventRecord(ctx->ev[0], ctx->stream)) != cudaSuccess)
+    if (with_events && (e = cudaEventRecord(ctx->ev[0], s)) != cudaSuccess)
         return cuda_fail(ctx, e, "qtm_run: cudaEventRecord");
     if (ntraj > 0) {
         KernelArgs a{};
@@ -596,29 +616,204 @@ qtm_status qtm_run_range(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64_t se
         a.jump_t = (double *)ctx->d_jump_t.p;
         a.jump_ch = (int *)ctx->d_jump_ch.p;
         if (ctx->precision == QTM_PREC_DF64)
-            e = qtm::launch_mcwf_df64(a, ctx->stream, &ctx->info);
+            e = qtm::launch_mcwf_df64(a, s, &ctx->info);
         else if (ctx->precision == QTM_PREC_C64)
-            e = qtm::launch_mcwf_c64(a, ctx->stream, &ctx->info);
+            e = qtm::launch_mcwf_c64(a, s, &ctx->info);
         else
-            e = qtm::launch_mcwf_c128(a, ctx->stream, &ctx->info);
+            e = qtm::launch_mcwf_c128(a, s, &ctx->info);
         if (e == cudaErrorInvalidValue)
             return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_run: no trajectory kernel fits this problem");
         if (e != cudaSuccess) return cuda_fail(ctx, e, "qtm_run: trajectory kernel launch");
     }
-    if ((e = cudaEventRecord(ctx->ev[1], ctx->stream)) != cudaSuccess)
+    if (with_events && (e = cudaEventRecord(ctx->ev[1], s)) != cudaSuccess)
         return cuda_fail(ctx, e, "qtm_run: cudaEventRecord");
     double *st = (double *)ctx->d_stats.p;
-    e = qtm::launch_ensemble_reduce((const double *)ctx->d_out.p, ntraj, (int)P, (double *)ctx->d_partial.p,
-                                    st, st + P, st + 2 * P, st + 3 * P, ctx->stream);
+    e = qtm::launch_ensemble_reduce((const double *)ctx->d_out.p, ntraj, (int)P, (double *)ctx->d_partial.p, st,
+                                    st + P, st + 2 * P, st + 3 * P, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qtm_run: ensemble reduction launch");
-    if ((e = cudaEventRecord(ctx->ev[2], ctx->stream)) != cudaSuccess)
+    if (with_events && (e = cudaEventRecord(ctx->ev[2], s)) != cudaSuccess)
         return cuda_fail(ctx, e, "qtm_run: cudaEventRecord");
+    return QTM_OK;
+}
+
+qtm_status qtm_run_range(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64_t seed)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_run: ctx is NULL");
+    ctx->err.clear();
+    if (first < 0 || ntraj < 0) return fail(ctx, QTM_ERR_ARG, "qtm_run: first and ntraj must be >= 0");
+    if (ntraj > ((int64_t)1 << 40)) return fail(ctx, QTM_ERR_ARG, "qtm_run: ntraj too large");
+    qtm_status st = reserve_run(ctx, ntraj);
+    if (st) return st;
+    if ((st = enqueue_run(ctx, first, ntraj, seed, ctx->stream, true))) return st;
     ctx->timed = true;
     ctx->last_ntraj = ntraj;
     return QTM_OK;
 }
 
+qtm_status qtm_run_batch(qtm_ctx *const *ctxs, const int64_t *ntraj, int32_t n, uint64_t seed)
+{
+    if (!ctxs || !ntraj || n < 1) return fail(nullptr, QTM_ERR_ARG, "qtm_run_batch: need n >= 1 contexts");
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return fail(nullptr, QTM_ERR_ARG, "qtm_run_batch: NULL context");
+        if (ntraj[i] < 0 || ntraj[i] > ((int64_t)1 << 40))
+            return fail(ctxs[i], QTM_ERR_ARG, "qtm_run_batch: ntraj out of range");
+        if (ctxs[i]->device != ctxs[0]->device)
+            return fail(ctxs[i], QTM_ERR_ARG, "qtm_run_batch: contexts on different devices");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return fail(ctxs[i], QTM_ERR_ARG, "qtm_run_batch: context listed twice");
+    }
+    for (int i = 0; i < n; ++i) {
+        ctxs[i]->err.clear();
+        qtm_status st = reserve_run(ctxs[i], ntraj[i]);
+        if (st) return st;
+    }
+    qtm_ctx *lead = ctxs[0];
+    cudaStream_t main = lead->stream;  // the graph runs here (may be the legacy stream)
+    cudaStream_t cap = nullptr;        // capture happens on a private stream
+    std::vector<cudaStream_t> branch(n, nullptr);
+    std::vector<cudaEvent_t> joins(n, nullptr), before(n, nullptr);
+    cudaEvent_t fork = nullptr, done = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    qtm_status st = QTM_OK;
+    cudaError_t e = cudaSuccess;
+    auto cleanup = [&]() {
+        if (graph) cudaGraphDestroy(graph);
+        if (exec) cudaGraphExecDestroy(exec);  // released once the launched work completes
+        for (auto &b : branch)
+            if (b) cudaStreamDestroy(b);
+        if (cap) cudaStreamDestroy(cap);
+        for (auto &j : joins)
+            if (j) cudaEventDestroy(j);
+        for (auto &j : before)
+            if (j) cudaEventDestroy(j);
+        if (fork) cudaEventDestroy(fork);
+        if (done) cudaEventDestroy(done);
+    };
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (!e) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    if (!e) e = cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    for (int i = 0; i < n && !e; ++i) {
+        e = cudaStreamCreateWithFlags(&branch[i], cudaStreamNonBlocking);
+        if (!e) e = cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming);
+        if (!e) e = cudaEventCreateWithFlags(&before[i], cudaEventDisableTiming);
+    }
+    if (e) {
+        cleanup();
+        return cuda_fail(lead, e, "qtm_run_batch: stream/event creation");
+    }
+    // one graph: every system's run on its own branch, all branches joined; the
+    // systems' persistent kernels overlap on the GPU
+    if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed)) || (e = cudaEventRecord(fork, cap))) {
+        cleanup();
+        return cuda_fail(lead, e, "qtm_run_batch: capture");
+    }
+    for (int i = 0; i < n && st == QTM_OK; ++i) {
+        if ((e = cudaStreamWaitEvent(branch[i], fork, 0))) break;
+        st = enqueue_run(ctxs[i], 0, ntraj[i], seed, branch[i], false);
+        if (st) break;
+        if ((e = cudaEventRecord(joins[i], branch[i])) || (e = cudaStreamWaitEvent(cap, joins[i], 0))) break;
+    }
+    cudaError_t ec = cudaStreamEndCapture(cap, &graph);
+    if (st == QTM_OK && e == cudaSuccess) e = ec;
+    if (st == QTM_OK && e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    // the launch follows earlier work queued on every context's own stream
+    for (int i = 1; i < n && st == QTM_OK && e == cudaSuccess; ++i)
+        if (ctxs[i]->stream != main) {
+            e = cudaEventRecord(before[i], ctxs[i]->stream);
+            if (!e) e = cudaStreamWaitEvent(main, before[i], 0);
+        }
+    if (st == QTM_OK && e == cudaSuccess) e = cudaGraphLaunch(exec, main);
+    if (st == QTM_OK && e == cudaSuccess) e = cudaEventRecord(done, main);
+    for (int i = 1; i < n && st == QTM_OK && e == cudaSuccess; ++i)
+        if (ctxs[i]->stream != main) e = cudaStreamWaitEvent(ctxs[i]->stream, done, 0);
+    cleanup();
+    if (st) return st;
+    if (e != cudaSuccess) return cuda_fail(lead, e, "qtm_run_batch: graph capture or launch");
+    for (int i = 0; i < n; ++i) {
+        ctxs[i]->timed = false;
+        ctxs[i]->last_ntraj = ntraj[i];
+    }
+    return QTM_OK;
+}
+
 qtm_status qtm_run(qtm_ctx *ctx, int64_t ntraj, uint64_t seed) { return qtm_run_range(ctx, 0, ntraj, seed); }
+
+// Re-uploads the packed operators (after repack).
+static qtm_status upload_ops(qtm_ctx *ctx)
+{
+    std::vector<unsigned char> vals_dev = encode_reals(ctx->reals, ctx->precision);
+    const size_t ib = ctx->ints.size() * sizeof(int), vb = vals_dev.size();
+    cudaError_t e;
+    if ((e = dev_reserve(ctx, ctx->d_ints, ib)) || (e = dev_reserve(ctx, ctx->d_vals, vb)))
+        return cuda_fail(ctx, e, "qtm_autotune: device allocation");
+    if ((e = cudaMemcpyAsync(ctx->d_ints.p, ctx->ints.data(), ib, cudaMemcpyHostToDevice, ctx->stream)) ||
+        (e = cudaMemcpyAsync(ctx->d_vals.p, vals_dev.data(), vb, cudaMemcpyHostToDevice, ctx->stream)) ||
+        (e = cudaStreamSynchronize(ctx->stream)))
+        return cuda_fail(ctx, e, "qtm_autotune: upload");
+    return QTM_OK;
+}
+
+qtm_status qtm_set_layout(qtm_ctx *ctx, int32_t group, int32_t rows)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_set_layout: ctx is NULL");
+    ctx->err.clear();
+    qtm::Layout cand[2];
+    const int nc = qtm::layout_candidates(ctx->n, cand);
+    for (int i = 0; i < nc; ++i)
+        if (cand[i].G == group && cand[i].R == rows) {
+            repack(ctx, cand[i]);
+            qtm_status st = upload_ops(ctx);
+            if (st) return st;
+            ctx->last_ntraj = -1;
+            return QTM_OK;
+        }
+    return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_set_layout: not a layout for this dimension");
+}
+
+qtm_status qtm_autotune(qtm_ctx *ctx, int64_t sample, uint64_t seed, int32_t *group, int32_t *rows)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_autotune: ctx is NULL");
+    ctx->err.clear();
+    if (sample < 1 || sample > ((int64_t)1 << 40)) return fail(ctx, QTM_ERR_ARG, "qtm_autotune: sample must be >= 1");
+    qtm::Layout cand[2];
+    const int nc = qtm::layout_candidates(ctx->n, cand);
+    if (nc < 1) return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_autotune: no layout for this dimension");
+    qtm_status st = reserve_run(ctx, sample);
+    if (st) return st;
+    float best = 0.f;
+    int best_i = -1;
+    for (int i = 0; i < nc; ++i) {
+        repack(ctx, cand[i]);
+        if ((st = upload_ops(ctx))) return st;
+        float ms = 0.f;
+        bool ok = true;
+        for (int rep = 0; rep < 2 && ok; ++rep) {  // first pass warms up
+            st = enqueue_run(ctx, 0, sample, seed, ctx->stream, true);
+            if (st == QTM_ERR_UNSUPPORTED) {
+                ok = false;  // shared memory of this layout does not fit
+                ctx->err.clear();
+                break;
+            }
+            if (st) return st;
+            cudaError_t e = cudaEventSynchronize(ctx->ev[2]);
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "qtm_autotune: timing");
+            if ((e = cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[2])) != cudaSuccess)
+                return cuda_fail(ctx, e, "qtm_autotune: timing");
+        }
+        if (ok && (best_i < 0 || ms < best)) {
+            best = ms;
+            best_i = i;
+        }
+    }
+    if (best_i < 0) return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_autotune: no layout fits");
+    repack(ctx, cand[best_i]);
+    if ((st = upload_ops(ctx))) return st;
+    ctx->last_ntraj = -1;  // the sample runs are not results
+    if (group) *group = cand[best_i].G;
+    if (rows) *rows = cand[best_i].R;
+    return QTM_OK;
+}
 
 static qtm_status sync_and_status(qtm_ctx *ctx)
 {

@@ -29,10 +29,25 @@ struct OpOffsets {
 };
 
 // Lanes per trajectory G and state rows per lane R for dimension n (n <= G R);
-// G = 0 when no register-resident layout fits.
+// G = 0 when no layout fits.
 struct Layout {
     int G, R;
 };
+
+// Layouts the autotuner may time for dimension n, default first.
+inline int layout_candidates(int n, Layout out[2])
+{
+    if (n <= 2) { out[0] = Layout{1, 2}; return 1; }
+    if (n <= 8) { out[0] = Layout{4, 2}; return 1; }
+    if (n <= 16) { out[0] = Layout{8, 2}; out[1] = Layout{4, 4}; return 2; }
+    if (n <= 32) { out[0] = Layout{16, 2}; out[1] = Layout{8, 4}; return 2; }
+    if (n <= 64) { out[0] = Layout{32, 2}; out[1] = Layout{16, 4}; return 2; }
+    if (n <= 128) { out[0] = Layout{64, 2}; out[1] = Layout{32, 4}; return 2; }
+    if (n <= 256) { out[0] = Layout{128, 2}; out[1] = Layout{64, 4}; return 2; }
+    if (n <= 512) { out[0] = Layout{256, 2}; out[1] = Layout{128, 4}; return 2; }
+    if (n <= 1024) { out[0] = Layout{256, 4}; return 1; }
+    return 0;
+}
 inline Layout layout_for_dim(int n)
 {
     if (n <= 2) return Layout{1, 2};
@@ -86,14 +101,28 @@ struct LaunchInfo {
 // values per trajectory must fit in shared memory).
 constexpr int kMaxDimSparse = 1024;
 
-// FP64 (complex128) trajectory kernel, CSR operators.  Chooses lanes per
-// trajectory and rows per lane from args.n; returns cudaErrorInvalidValue when
-// no instantiation fits.
-cudaError_t launch_mcwf_c128(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
-// Same kernel with double-float vectors (FP64-class precision on the FP32 pipe).
-cudaError_t launch_mcwf_df64(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
-// Same kernel with complex64 vectors and double-float norms.
-cudaError_t launch_mcwf_c64(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+// The trajectory kernel for the layout args.G x args.R, in complex128,
+// double-float or complex64 arithmetic (single-warp layouts in *_small,
+// multi-warp layouts in *_large); cudaErrorInvalidValue when no instantiation
+// exists for the layout or its shared memory does not fit.
+cudaError_t launch_mcwf_c128_small(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+cudaError_t launch_mcwf_c128_large(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+cudaError_t launch_mcwf_df64_small(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+cudaError_t launch_mcwf_df64_large(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+cudaError_t launch_mcwf_c64_small(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+cudaError_t launch_mcwf_c64_large(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+inline cudaError_t launch_mcwf_c128(const KernelArgs &a, cudaStream_t s, LaunchInfo *i)
+{
+    return a.G <= 32 ? launch_mcwf_c128_small(a, s, i) : launch_mcwf_c128_large(a, s, i);
+}
+inline cudaError_t launch_mcwf_df64(const KernelArgs &a, cudaStream_t s, LaunchInfo *i)
+{
+    return a.G <= 32 ? launch_mcwf_df64_small(a, s, i) : launch_mcwf_df64_large(a, s, i);
+}
+inline cudaError_t launch_mcwf_c64(const KernelArgs &a, cudaStream_t s, LaunchInfo *i)
+{
+    return a.G <= 32 ? launch_mcwf_c64_small(a, s, i) : launch_mcwf_c64_large(a, s, i);
+}
 
 // Ensemble reduction of out[ntraj][P] into sums, sums of squares, mean and
 // standard error, in a fixed summation order (bitwise reproducible).

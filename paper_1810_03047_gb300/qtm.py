@@ -40,7 +40,8 @@ QTM_FLAG_RECORD_JUMPS = 1
 EXPORTS = ["qtm_set_allocator", "qtm_create", "qtm_run", "qtm_run_range", "qtm_expect", "qtm_sums",
            "qtm_sums_device",
            "qtm_traj_expect", "qtm_jumps", "qtm_stats", "qtm_last_error", "qtm_status_string",
-           "qtm_destroy", "qtm_version", "qtm_ensemble_reduce_static"]
+           "qtm_destroy", "qtm_version", "qtm_ensemble_reduce_static", "qtm_run_batch", "qtm_autotune",
+           "qtm_set_layout"]
 
 
 class QtmError(RuntimeError):
@@ -108,6 +109,13 @@ def lib():
             L.qtm_ensemble_reduce_static.argtypes = [ct.c_void_p, ct.c_int64, ct.c_int32, ct.c_void_p,
                                                      ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]
             L.qtm_ensemble_reduce_static.restype = ct.c_int
+            L.qtm_run_batch.argtypes = [ct.POINTER(ct.c_void_p), ct.POINTER(ct.c_int64), ct.c_int32, ct.c_uint64]
+            L.qtm_run_batch.restype = ct.c_int
+            L.qtm_autotune.argtypes = [ct.c_void_p, ct.c_int64, ct.c_uint64, ct.POINTER(ct.c_int32),
+                                       ct.POINTER(ct.c_int32)]
+            L.qtm_autotune.restype = ct.c_int
+            L.qtm_set_layout.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32]
+            L.qtm_set_layout.restype = ct.c_int
             for name in ("qtm_create", "qtm_run", "qtm_run_range", "qtm_expect", "qtm_sums", "qtm_sums_device",
                          "qtm_traj_expect", "qtm_jumps", "qtm_stats", "qtm_set_allocator"):
                 getattr(L, name).restype = ct.c_int
@@ -256,6 +264,28 @@ def qtm_run(ctx: Ctx, ntraj: int, seed: int):
 def qtm_run_range(ctx: Ctx, first: int, ntraj: int, seed: int):
     _check(lib().qtm_run_range(ctx.handle, int(first), int(ntraj), int(seed)), ctx)
     ctx.last_ntraj = int(ntraj)
+
+
+def qtm_run_batch(ctxs, ntrajs, seed: int):
+    """Runs several contexts' ensembles in one CUDA graph (see qtm.h)."""
+    arr = (ct.c_void_p * len(ctxs))(*[c.handle for c in ctxs])
+    nt = (ct.c_int64 * len(ctxs))(*[int(x) for x in ntrajs])
+    _check(lib().qtm_run_batch(arr, nt, len(ctxs), int(seed)), ctxs[0])
+    for c, n in zip(ctxs, ntrajs):
+        c.last_ntraj = int(n)
+
+
+def qtm_autotune(ctx: Ctx, sample: int, seed: int = 1):
+    """Times the available lane layouts on `sample` trajectories and keeps the fastest;
+    returns (threads per trajectory, rows per thread)."""
+    g = ct.c_int32()
+    r = ct.c_int32()
+    _check(lib().qtm_autotune(ctx.handle, int(sample), int(seed), ct.byref(g), ct.byref(r)), ctx)
+    return g.value, r.value
+
+
+def qtm_set_layout(ctx: Ctx, group: int, rows: int):
+    _check(lib().qtm_set_layout(ctx.handle, int(group), int(rows)), ctx)
 
 
 def _dp(a):

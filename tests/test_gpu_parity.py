@@ -263,3 +263,84 @@ def test_complex64_two_level_steady_state(orc):
     g = gpu_run(prob, prob.ntraj, precision=Q.QTM_PREC_C64)
     L, _ = orc.lindblad(prob, 1e-10, 1e-12)
     _within_statistics(g["mean"], g["se"], L, prob.ntraj)
+
+
+def test_batch_equals_individual_runs():
+    """qtm_run_batch (one CUDA graph, one branch per system) gives bitwise the same
+    per-trajectory values as running each context alone."""
+    probs = [S.two_level_driven(), S.jaynes_cummings_driven(), S.ising_chain(7)]
+    ntrajs = [300, 130, 37]
+    alone = [gpu_run(p, n, seed=1, record=0, precision=Q.QTM_PREC_DF64) for p, n in zip(probs, ntrajs)]
+    ctxs = [Q.qtm_create(p, precision=Q.QTM_PREC_DF64) for p in probs]
+    Q.qtm_run_batch(ctxs, ntrajs, 1)
+    for c, ref in zip(ctxs, alone):
+        np.testing.assert_array_equal(Q.qtm_traj_expect(c), ref["obs"])
+        mean, se = Q.qtm_expect(c)
+        np.testing.assert_array_equal(mean, ref["mean"])
+        np.testing.assert_array_equal(se, ref["se"])
+        Q.qtm_destroy(c)
+
+
+@pytest.mark.parametrize("prec", [p[1] for p in PRECS], ids=[p[0] for p in PRECS])
+def test_batched_ising_ensemble_parity(orc, prec):
+    """The uneven batched workload (transverse-field Ising chains L = 6..10, N = 64..1024)
+    in one graph launch, each system trajectory by trajectory against the oracle."""
+    Ls = [6, 7, 8, 9, 10]
+    counts = [48, 24, 12, 8, 6]
+    probs = [S.ising_chain(L) for L in Ls]
+    ctxs = [Q.qtm_create(p, precision=prec, record_jumps=MAXJ) for p in probs]
+    Q.qtm_run_batch(ctxs, counts, 7)
+    for c, p, n in zip(ctxs, probs, counts):
+        mean, se = Q.qtm_expect(c)
+        g = dict(mean=mean, se=se, obs=Q.qtm_traj_expect(c))
+        g["n_jumps"], g["jump_t"], g["jump_ch"] = Q.qtm_jumps(c)
+        compare(g, oracle_run(orc, p, n, seed=7), n, precision=prec)
+        Q.qtm_destroy(c)
+
+
+def test_autotune_keeps_parity(orc):
+    prob = S.jaynes_cummings_driven()
+    ctx = Q.qtm_create(prob, precision=Q.QTM_PREC_DF64, record_jumps=MAXJ)
+    G, R = Q.qtm_autotune(ctx, 2048, 3)
+    assert (G, R) in {(32, 2), (16, 4)}
+    Q.qtm_run(ctx, 127, 1)
+    mean, se = Q.qtm_expect(ctx)
+    g = dict(mean=mean, se=se, obs=Q.qtm_traj_expect(ctx))
+    g["n_jumps"], g["jump_t"], g["jump_ch"] = Q.qtm_jumps(ctx)
+    st = Q.qtm_stats(ctx)
+    assert (st["kernel_group"], st["kernel_rows"]) == (G, R)
+    Q.qtm_destroy(ctx)
+    compare(g, oracle_run(orc, prob, 127), 127, precision=Q.QTM_PREC_DF64)
+
+
+@pytest.mark.parametrize("layout_n", [12, 40, 100, 200, 400])
+def test_alternative_layouts_keep_parity(orc, layout_n):
+    """Every candidate lane layout gives the oracle's trajectories: random sparse
+    systems of dimension 12, 40, 100, 200 and 400, run in each layout the
+    autotuner may choose for them (both the 2-row and the 4-row layouts)."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(layout_n)
+    n = layout_n
+    # a random sparse Hermitian H (about 4 entries per row) and two sparse channels
+    A = sp.random(n, n, density=4.0 / n, random_state=rng, data_rvs=lambda k: rng.standard_normal(k))
+    H = S._csr((A + A.T) * 0.5 + 1j * (A - A.T) * 0.25)
+    C = [S._csr(sp.random(n, n, density=1.5 / n, random_state=rng, data_rvs=lambda k: 0.3 * rng.standard_normal(k))),
+         S._csr(0.2 * S.destroy(n))]
+    psi0 = np.zeros(n, complex)
+    psi0[0] = 1.0
+    prob = S.Problem("random_sparse", H, C, [S._csr(sp.diags(np.arange(n) / n))], psi0,
+                     np.linspace(0, 5, 51), ntraj=32, seed=2)
+    o = oracle_run(orc, prob, 32)
+    layouts = {12: [(8, 2), (4, 4)], 40: [(32, 2), (16, 4)], 100: [(64, 2), (32, 4)],
+               200: [(128, 2), (64, 4)], 400: [(256, 2), (128, 4)]}[n]
+    for prec in (Q.QTM_PREC_C128, Q.QTM_PREC_DF64):
+        for G, R in layouts:
+            ctx = Q.qtm_create(prob, precision=prec, record_jumps=MAXJ)
+            Q.qtm_set_layout(ctx, G, R)
+            Q.qtm_run(ctx, 32, 2)
+            mean, se = Q.qtm_expect(ctx)
+            g = dict(mean=mean, se=se, obs=Q.qtm_traj_expect(ctx))
+            g["n_jumps"], g["jump_t"], g["jump_ch"] = Q.qtm_jumps(ctx)
+            assert (Q.qtm_stats(ctx)["kernel_group"], Q.qtm_stats(ctx)["kernel_rows"]) == (G, R)
+            Q.qtm_destroy(ctx)
+            compare(g, o, 32, precision=prec)
