@@ -419,14 +419,14 @@ def ising_batch(Q, torch, stream, world, rank, dist):
     ref = [Q.qtm_create(p, stream=sid, precision=Q.QTM_PREC_C128) for p in probs]
     fast = [Q.qtm_create(p, stream=sid, precision=Q.QTM_PREC_DF64) for p in probs]
     layouts = [Q.qtm_autotune(c, min(n, 4096), 7) for c, n in zip(fast, counts)]
-    Q.qtm_run_batch(ref, counts, 7)
+    Q.qtm_run_batch(ref, counts, 7, firsts)
     ref_means = [Q.qtm_expect(c)[0] for c in ref]
     ref_ms = []
     for _ in range(2):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        Q.qtm_run_batch(fast, counts, 7)
+        Q.qtm_run_batch(fast, counts, 7, firsts)
         e1.record(stream)
         e1.synchronize()
         ref_ms.append(e0.elapsed_time(e1))

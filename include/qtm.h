@@ -173,8 +173,8 @@ qtm_status qtm_run(qtm_ctx *ctx, int64_t ntraj, uint64_t seed);
  * a single larger run. */
 qtm_status qtm_run_range(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64_t seed);
 
-/* Runs several ensembles at once: context i runs its trajectories 0 .. ntraj[i]-1
- * keyed by seed.  All runs are captured into one CUDA graph -- each system's
+/* Runs several ensembles at once: context i runs global trajectory ids
+ * first[i] .. first[i]+ntraj[i]-1 (first may be NULL: all zero) keyed by seed.  All runs are captured into one CUDA graph -- each system's
  * persistent kernel and reduction on its own branch -- and launched on the
  * stream of ctxs[0]; the other contexts' streams wait for that launch, so each
  * context's results are read with qtm_expect as usual.  Systems of different
@@ -182,7 +182,8 @@ qtm_status qtm_run_range(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64_t se
  * submission, and the tail of one system overlaps the others.  All contexts must
  * be on the same device and distinct.  qtm_stats of a batched run reports no
  * kernel times (kernel_ms = 0). */
-qtm_status qtm_run_batch(qtm_ctx *const *ctxs, const int64_t *ntraj, int32_t n, uint64_t seed);
+qtm_status qtm_run_batch(qtm_ctx *const *ctxs, const int64_t *first, const int64_t *ntraj, int32_t n,
+                         uint64_t seed);
 
 /* Times the lane layouts available for the context's dimension (threads per
  * trajectory x state rows per thread, see qtm_stats_t.kernel_group / kernel_rows)

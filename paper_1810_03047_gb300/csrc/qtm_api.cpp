@@ -650,13 +650,15 @@ qtm_status qtm_run_range(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64_t se
     return QTM_OK;
 }
 
-qtm_status qtm_run_batch(qtm_ctx *const *ctxs, const int64_t *ntraj, int32_t n, uint64_t seed)
+qtm_status qtm_run_batch(qtm_ctx *const *ctxs, const int64_t *first, const int64_t *ntraj, int32_t n,
+                         uint64_t seed)
 {
     if (!ctxs || !ntraj || n < 1) return fail(nullptr, QTM_ERR_ARG, "qtm_run_batch: need n >= 1 contexts");
     for (int i = 0; i < n; ++i) {
         if (!ctxs[i]) return fail(nullptr, QTM_ERR_ARG, "qtm_run_batch: NULL context");
         if (ntraj[i] < 0 || ntraj[i] > ((int64_t)1 << 40))
             return fail(ctxs[i], QTM_ERR_ARG, "qtm_run_batch: ntraj out of range");
+        if (first && first[i] < 0) return fail(ctxs[i], QTM_ERR_ARG, "qtm_run_batch: first must be >= 0");
         if (ctxs[i]->device != ctxs[0]->device)
             return fail(ctxs[i], QTM_ERR_ARG, "qtm_run_batch: contexts on different devices");
         for (int j = 0; j < i; ++j)
@@ -710,7 +712,7 @@ qtm_status qtm_run_batch(qtm_ctx *const *ctxs, const int64_t *ntraj, int32_t n, 
     }
     for (int i = 0; i < n && st == QTM_OK; ++i) {
         if ((e = cudaStreamWaitEvent(branch[i], fork, 0))) break;
-        st = enqueue_run(ctxs[i], 0, ntraj[i], seed, branch[i], false);
+        st = enqueue_run(ctxs[i], first ? first[i] : 0, ntraj[i], seed, branch[i], false);
         if (st) break;
         if ((e = cudaEventRecord(joins[i], branch[i])) || (e = cudaStreamWaitEvent(cap, joins[i], 0))) break;
     }

@@ -109,7 +109,8 @@ def lib():
             L.qtm_ensemble_reduce_static.argtypes = [ct.c_void_p, ct.c_int64, ct.c_int32, ct.c_void_p,
                                                      ct.c_void_p, ct.c_void_p, ct.c_void_p, ct.c_void_p]
             L.qtm_ensemble_reduce_static.restype = ct.c_int
-            L.qtm_run_batch.argtypes = [ct.POINTER(ct.c_void_p), ct.POINTER(ct.c_int64), ct.c_int32, ct.c_uint64]
+            L.qtm_run_batch.argtypes = [ct.POINTER(ct.c_void_p), ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int64),
+                                        ct.c_int32, ct.c_uint64]
             L.qtm_run_batch.restype = ct.c_int
             L.qtm_autotune.argtypes = [ct.c_void_p, ct.c_int64, ct.c_uint64, ct.POINTER(ct.c_int32),
                                        ct.POINTER(ct.c_int32)]
@@ -266,11 +267,12 @@ def qtm_run_range(ctx: Ctx, first: int, ntraj: int, seed: int):
     ctx.last_ntraj = int(ntraj)
 
 
-def qtm_run_batch(ctxs, ntrajs, seed: int):
+def qtm_run_batch(ctxs, ntrajs, seed: int, firsts=None):
     """Runs several contexts' ensembles in one CUDA graph (see qtm.h)."""
     arr = (ct.c_void_p * len(ctxs))(*[c.handle for c in ctxs])
     nt = (ct.c_int64 * len(ctxs))(*[int(x) for x in ntrajs])
-    _check(lib().qtm_run_batch(arr, nt, len(ctxs), int(seed)), ctxs[0])
+    fs = (ct.c_int64 * len(ctxs))(*[int(x) for x in firsts]) if firsts is not None else None
+    _check(lib().qtm_run_batch(arr, fs, nt, len(ctxs), int(seed)), ctxs[0])
     for c, n in zip(ctxs, ntrajs):
         c.last_ntraj = int(n)
 

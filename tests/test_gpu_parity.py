@@ -265,6 +265,16 @@ def test_complex64_two_level_steady_state(orc):
     _within_statistics(g["mean"], g["se"], L, prob.ntraj)
 
 
+def test_batch_with_offsets_equals_ranges(orc):
+    """A batch entry with a first id runs exactly those global trajectory ids."""
+    prob = S.jaynes_cummings_driven()
+    ref = gpu_run(prob, 40, first=25, record=0, precision=Q.QTM_PREC_DF64)
+    ctx = Q.qtm_create(prob, precision=Q.QTM_PREC_DF64)
+    Q.qtm_run_batch([ctx], [40], 1, firsts=[25])
+    np.testing.assert_array_equal(Q.qtm_traj_expect(ctx), ref["obs"])
+    Q.qtm_destroy(ctx)
+
+
 def test_batch_equals_individual_runs():
     """qtm_run_batch (one CUDA graph, one branch per system) gives bitwise the same
     per-trajectory values as running each context alone."""
