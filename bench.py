@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-proposal", action="store_true",
+                    help="skip the learned jump-time proposal measurement (200,000 JC trajectories)")
     ap.add_argument("--no-ising", action="store_true",
                     help="skip the batched Ising-chain measurement (L = 6..10 in one CUDA graph)")
     ap.add_argument("--only", choices=["c128", "df64", "c64"], default=None,
@@ -391,6 +393,9 @@ def main():
     if not args.no_ising:
         line["ising_batch"] = ising_batch(Q, torch, stream, world, rank, dist)
         line["gpu_launches"] += line["ising_batch"].pop("launches")
+    if not args.no_proposal:
+        line["learned_proposal"] = learned_proposal(Q, torch, stream, world, rank, dist)
+        line["gpu_launches"] += line["learned_proposal"].pop("launches")
     if world == 1 and rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(prob, args.cpu_seconds, rank)
     if rank == 0:
@@ -442,6 +447,61 @@ def ising_batch(Q, torch, stream, world, rank, dist):
                         "one CUDA-graph launch", "precision": "df64",
             "value": world * sum(counts) / (float(t.item()) / 1e3), "unit": UNIT, "ms_per_step": float(t.item()),
             "observable_error": err, "layouts": [list(x) for x in layouts], "launches": 2 * 5 * 5}
+
+
+def learned_proposal(Q, torch, stream, world, rank, dist, ntraj=200000):
+    """The learned jump-time proposal on the Jaynes-Cummings workload: about 10^6
+    (features -> time left to the jump) pairs from 12,000 trajectories of the
+    plain method (seed 11), the 6-64-64-1 network trained on the GPU, then 200,000
+    trajectories (seed 1) timed with the plain double-float kernel and with the
+    proposal kernel (network inference fused in the step loop; the root find
+    still decides every jump).  Steps per trajectory, trajectories/s and the
+    ensemble difference between the two are reported."""
+    from paper_1810_03047_gb300 import shards
+    prob, _, _ = workload(ntraj)
+    sid = int(stream.cuda_stream)
+    first, count = shards.shard(world * ntraj, world, rank)
+    ctx = Q.qtm_create(prob, stream=sid, precision=Q.QTM_PREC_DF64)
+    t0 = time.perf_counter()
+    npairs = Q.qtm_proposal_collect(ctx, 12000, 11, stride=8, max_per_traj=96)
+    t1 = time.perf_counter()
+    steps = 2000
+    loss, base = Q.qtm_proposal_train(ctx, steps=steps, batch=8192, lr=2e-3, seed=11)
+    t2 = time.perf_counter()
+    Q.qtm_run_range(ctx, first, min(count, 20000), prob.seed)  # warm-up of both kernels
+    Q.qtm_proposal_enable(ctx, True, 0.05)
+    Q.qtm_run_range(ctx, first, min(count, 20000), prob.seed)
+    res = {}
+    for on in (False, True):
+        Q.qtm_proposal_enable(ctx, on, 0.05)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Q.qtm_run_range(ctx, first, count, prob.seed)
+        e1.record(stream)
+        e1.synchronize()
+        t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        st = Q.qtm_stats(ctx)
+        res[on] = {"ms": float(t.item()), "mean": Q.qtm_expect(ctx)[0],
+                   "steps": (st["accepted"] + st["rejected"]) / count, "jumps": st["jumps"] / count}
+    Q.qtm_destroy(ctx)
+    off, on = res[False], res[True]
+    return {"workload": f"damped driven Jaynes-Cummings (N=60), {world * ntraj} trajectories (seed 1); "
+                        f"network trained on {npairs} pairs from 12,000 trajectories (seed 11)",
+            "precision": "df64", "unit": UNIT,
+            "value": world * ntraj / (on["ms"] / 1e3), "plain_value": world * ntraj / (off["ms"] / 1e3),
+            "steps_per_trajectory": on["steps"], "plain_steps_per_trajectory": off["steps"],
+            "step_saving": (off["steps"] - on["steps"]) / off["steps"],
+            "jumps_per_trajectory": on["jumps"], "plain_jumps_per_trajectory": off["jumps"],
+            "observable_error_vs_plain": float(np.abs(on["mean"] - off["mean"]).max()),
+            "train": {"pairs": npairs, "steps": steps, "batch": 8192, "loss": loss, "loss_rate_estimate": base,
+                      "collect_s": t1 - t0, "train_s": t2 - t1},
+            "launches": 5 + 3 * steps + 1 + 4 * 5}
 
 
 if __name__ == "__main__":

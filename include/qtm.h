@@ -261,6 +261,63 @@ qtm_status qtm_traj_expect(qtm_ctx *ctx, double *out);
  * max_jumps_recorded jump times and channel indices (unused slots: NaN / -1). */
 qtm_status qtm_jumps(qtm_ctx *ctx, int32_t *n_jumps, double *jump_t, int32_t *jump_ch);
 
+/* ---------------------------------------------------------------------------
+ * Learned jump-time proposal.  A small network (6 -> 64 -> 64 -> 1, SiLU, FP32)
+ * predicts the time left until the trajectory's norm falls to its threshold r
+ * (the crossing of Algorithm 1, step (B)) from cheap features of the state: the
+ * decay rate Gamma = <sum_n C_n^dag C_n> (from the norm ratio over the last
+ * step), its slope, <psi|psi>, log r, and the latest output values of the first
+ * two observables.  Its output y corrects the constant-rate estimate:
+ * time left = log(<psi|psi> / r) / Gamma * exp(y).  When enabled, a step that
+ * would contain the predicted crossing is shortened to end a fraction `margin`
+ * past it, so less of that step is discarded at the jump.  The exact root find
+ * of the continuous extension still decides every jump; only the step sequence
+ * changes (so results move by the integration tolerance, not more).  The paper
+ * has no such component: it is the learned part of this library's design.
+ * Supported for QTM_PREC_C128 and QTM_PREC_DF64 at dimension <= 64 (the
+ * single-warp lane layouts, where it is compiled into separate kernels so the
+ * plain kernels carry none of it); other contexts get QTM_ERR_UNSUPPORTED from
+ * qtm_proposal_collect and from qtm_proposal_enable(on != 0).
+ * ------------------------------------------------------------------------- */
+
+/* Floats of a network's parameter block: W1[64][6], b1[64], W2[64][64], b2[64],
+ * w3[64], b3, feature means[6], feature scales[6]. */
+#define QTM_PROPOSAL_FLOATS 4685
+
+/* Runs trajectories 0 .. ntraj-1 of the plain method (proposal off) and records,
+ * every `stride` accepted steps and at most max_per_traj times per trajectory,
+ * the 6 raw features and the time left to the next jump; records of a
+ * trajectory's last jump interval (no jump followed) are dropped.  Keeps the
+ * pairs for qtm_proposal_train; *npairs (may be NULL) = their number.
+ * Synchronises; the run's observables are available as after qtm_run. */
+qtm_status qtm_proposal_collect(qtm_ctx *ctx, int64_t ntraj, uint64_t seed, int32_t stride,
+                                int32_t max_per_traj, int64_t *npairs);
+
+/* Copies up to `capacity` collected pairs: features [capacity][6] (raw), dt [capacity]. */
+qtm_status qtm_proposal_pairs(qtm_ctx *ctx, float *features, float *dt, int64_t capacity);
+
+/* Trains the network on the collected pairs with the library's GPU kernels:
+ * features standardised, targets y = log(dt / constant-rate estimate), mean
+ * squared error, Adam (learning rate lr), `steps` minibatches of `batch` pairs of
+ * a shuffled order (shuffle and Glorot initialisation from `seed`).  *loss (may
+ * be NULL) = final mean squared error over all pairs; *loss_rate_estimate (may be
+ * NULL) = the same error of the constant-rate estimate alone (y = 0). */
+qtm_status qtm_proposal_train(qtm_ctx *ctx, int32_t steps, int32_t batch, float lr, uint64_t seed,
+                              float *loss, float *loss_rate_estimate);
+
+/* Loads / reads a parameter block of QTM_PROPOSAL_FLOATS floats (host memory). */
+qtm_status qtm_proposal_set(qtm_ctx *ctx, const float *params);
+qtm_status qtm_proposal_get(qtm_ctx *ctx, float *params);
+
+/* Turns the proposal on (on != 0) or off for later runs; margin in (0, 1). */
+qtm_status qtm_proposal_enable(qtm_ctx *ctx, int32_t on, float margin);
+
+/* Mean squared error and its gradient with respect to the first 4673 parameters
+ * for standardised inputs x[n][6] and targets t[n], computed by the training
+ * kernels on the current device (host pointers; for checking the kernels). */
+qtm_status qtm_mlp_loss_grad(const float *params, const float *x, const float *t, int64_t n, float *loss,
+                             float *grad);
+
 /* Counters of the last run (synchronises). */
 qtm_status qtm_stats(qtm_ctx *ctx, qtm_stats_t *out);
 

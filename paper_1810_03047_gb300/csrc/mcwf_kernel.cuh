@@ -38,6 +38,7 @@
 //       of the accepted step.
 #pragma once
 
+#include "proposal.cuh"
 #include "qtm_arith.cuh"
 #include "qtm_device.cuh"
 #include "qtm_launch.h"
@@ -145,10 +146,11 @@ __device__ __noinline__ void dense_rows(const Coefs<Ar> &C, const Lanes<Ar, G, R
 
 // Output j: Re<y|A_k|y>/<y|y> for every observable, written by lane 0.  y is in
 // the exchange half `y` and the group has synchronised after writing it.
+// When obs is not NULL, lane 0 also stores the first two values there as floats.
 template <class Ar, int G, int R>
 __device__ __noinline__ void record_outputs(const KernelArgs &a, Group<G> g, const int *si,
                                             const typename Ar::real *sv, const typename Ar::cplx *y, int j,
-                                            double *out)
+                                            double *out, float *obs)
 {
     using cplx = typename Ar::cplx;
     typename Ar::red nn = Ar::rzero();
@@ -168,8 +170,122 @@ __device__ __noinline__ void record_outputs(const KernelArgs &a, Group<G> g, con
             if (row < a.n) ev = Ar::radd(ev, Ar::dot_re(y[row], ay));
         }
         ev = Ar::rsum(g, ev);
-        if (g.gl == 0) out[(size_t)j * a.n_obs + k] = Ar::ratio(ev, nn);
+        const double value = Ar::ratio(ev, nn);
+        if (g.gl == 0) {
+            out[(size_t)j * a.n_obs + k] = value;
+            if (obs && k < 2) obs[k] = (float)value;
+        }
     }
+}
+
+// The learned proposal's network on features f (raw), evaluated by the group:
+// thread gl computes hidden units gl, gl + G, ... of each layer; the first
+// layer's activations pass through the group's 64-float scratch.
+template <int G>
+__device__ __noinline__ float mlp_eval(Group<G> g, const float *__restrict__ P, const float *f, float *h)
+{
+    g.sync();  // f was written by lane 0
+    float x[kMlpIn];
+#pragma unroll
+    for (int i = 0; i < kMlpIn; ++i) x[i] = (f[i] - P[kOffMu + i]) / P[kOffSd + i];
+    for (int j = g.gl; j < kMlpHidden; j += G) {
+        float z = P[kOffB1 + j];
+#pragma unroll
+        for (int i = 0; i < kMlpIn; ++i) z = fmaf(P[kOffW1 + j * kMlpIn + i], x[i], z);
+        h[j] = silu(z);
+    }
+    g.sync();
+    float acc = 0.f;
+    for (int k = g.gl; k < kMlpHidden; k += G) {
+        float z = P[kOffB2 + k];
+        for (int j = 0; j < kMlpHidden; ++j) z = fmaf(P[kOffW2 + k * kMlpHidden + j], h[j], z);
+        acc = fmaf(P[kOffW3 + k], silu(z), acc);
+    }
+    acc = g.sum(acc);
+    g.sync();
+    return acc + P[kOffB3];
+}
+
+// Per-trajectory state of the learned proposal, kept in shared memory beside the
+// network's scratch so that it takes no registers in the step loop.  Lane 0 alone
+// writes it; the other lanes read it only after a group barrier.
+struct PropState {
+    float f[kMlpIn];   // features for the next step: Gamma, dGamma/dt, <psi|psi>, log r, two outputs
+    float tmid;        // midpoint of the last accepted step, relative to the last jump
+    float est;         // constant-rate estimate of the time left
+    int rec_n, rec_open;
+    double t_jump;     // time of the last jump (or the start)
+    double h_ctrl;     // the controller's step when a proposed step replaced it
+};
+constexpr int kPropStride = kMlpHidden * 4 + (int)((sizeof(PropState) + 15) & ~size_t(15));
+
+static __device__ __forceinline__ float *prop_records(const KernelArgs &a, long long il)
+{
+    return a.rec_stride > 0 ? a.rec + (size_t)il * a.rec_max * kRecFloats : nullptr;
+}
+
+// (lane 0) a fresh jump interval starting at t with threshold r
+static __device__ __forceinline__ void prop_interval(PropState *P, double t, double r)
+{
+    P->f[0] = -1.f;
+    P->f[1] = 0.f;
+    P->f[2] = 1.f;
+    P->f[3] = __logf((float)r);
+    P->tmid = 0.f;
+    P->t_jump = t;
+}
+
+// Before a step of size h at time t: stores a training record when one is due
+// and, with a network loaded and the crossing near (constant-rate estimate within
+// three steps), returns the proposed step ending a fraction prop_margin past the
+// predicted crossing (0 when there is none).  Every lane gets the same value.
+template <int G>
+__device__ __noinline__ double prop_propose(const KernelArgs &a, Group<G> g, PropState *P, float *hscratch,
+                                            long long il, unsigned long long n_acc, double t, double h)
+{
+    int want = 0;
+    if (g.gl == 0 && P->f[0] > 0.f) {
+        float *rec = prop_records(a, il);
+        if (rec && P->rec_n < a.rec_max && n_acc % a.rec_stride == 0) {
+            float *q = rec + (size_t)P->rec_n * kRecFloats;
+            for (int i = 0; i < kMlpIn; ++i) q[i] = P->f[i];
+            q[6] = (float)(t - P->t_jump);
+            ++P->rec_n;
+        }
+        P->est = (__logf(P->f[2]) - P->f[3]) / P->f[0];
+        want = a.mlp != nullptr && P->est < 3.f * (float)h;
+    }
+    if (!a.mlp) return 0.0;
+    if (!g.bcast0(want)) return 0.0;
+    const float y = mlp_eval<G>(g, a.mlp, P->f, hscratch);
+    const double hp = (double)(P->est * __expf(y) * (1.f + a.prop_margin));
+    return (hp < h && hp > 1e-3 * h) ? hp : 0.0;
+}
+
+// (lane 0) after an accepted step from t of size h ending with norm nn: the decay
+// rate over the step from the norm ratio, and its slope against the last step's
+static __device__ __noinline__ void prop_accepted(PropState *P, double nn, double t, double h)
+{
+    const float nnf = (float)nn, hf = (float)h;
+    const float gam = -__logf(nnf / P->f[2]) / hf;
+    const float tmid = (float)(t - P->t_jump) + 0.5f * hf;
+    P->f[1] = P->f[0] > 0.f ? (gam - P->f[0]) / (tmid - P->tmid) : 0.f;
+    P->f[0] = gam;
+    P->f[2] = nnf;
+    P->tmid = tmid;
+}
+
+// (lane 0) at a jump at tau: the interval's records get their time left, and the
+// next interval starts with threshold r
+static __device__ __noinline__ void prop_jumped(const KernelArgs &a, PropState *P, long long il, double tau, double r)
+{
+    float *rec = prop_records(a, il);
+    if (rec) {
+        const float left = (float)(tau - P->t_jump);
+        for (int q = P->rec_open; q < P->rec_n; ++q) rec[(size_t)q * kRecFloats + 7] = left - rec[(size_t)q * kRecFloats + 6];
+        P->rec_open = P->rec_n;
+    }
+    prop_interval(P, tau, r);
 }
 
 // First theta in (0, 1] where ||y(theta)||^2 = r.  ||y(theta)||^2 = sum_s P_s theta^s
@@ -306,10 +422,10 @@ __device__ __noinline__ int apply_jump(const KernelArgs &a, Group<G> g, const in
     return ch;
 }
 
-template <class Ar, int G, int R>
+template <class Ar, int G, int R, bool PROP>
 __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int *si,
                                const typename Ar::real *sv, const Coefs<Ar> &C, Lanes<Ar, G, R> &L,
-                               long long il)
+                               float *hscratch, PropState *P, long long il)
 {
     using cplx = typename Ar::cplx;
     const int n = a.n;
@@ -340,8 +456,18 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
     double rk, ck;
     jump_draws(a.seed, traj, k, rk, ck);
     double t = a.t[0];
-    record_outputs<Ar, G, R>(a, g, si, sv, b, 0, out);
+    // learned proposal: its features live in P (FP32: the FP64 pipe is the scarce one)
+    float *obs = nullptr;
+    if constexpr (PROP) {
+        if (gl == 0) {
+            P->rec_n = P->rec_open = 0;
+            prop_interval(P, t, rk);
+        }
+        obs = P->f + 4;
+    }
+    record_outputs<Ar, G, R>(a, g, si, sv, b, 0, out, obs);
     int j = 1;
+    bool proposed = false;
     spmv_rows<Ar, G, R>(M, b, L.kq(0), gl, n);
     ++n_rhs;
 
@@ -409,7 +535,7 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
                 if (row < n) b[row] = psi[row];
             }
             g.sync();
-            for (; j < a.n_t; ++j) record_outputs<Ar, G, R>(a, g, si, sv, b, j, out);
+            for (; j < a.n_t; ++j) record_outputs<Ar, G, R>(a, g, si, sv, b, j, out, obs);
             break;
         }
         if (attempts >= a.max_steps) {
@@ -424,6 +550,16 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
         if (h < 1e-14 * fmax(1.0, fabs(t))) {
             status = 5;
             break;
+        }
+        if constexpr (PROP) {
+            proposed = false;
+            const double hp = prop_propose<G>(a, g, P, hscratch, il, n_acc, t, h);
+            if (hp > 0.0) {
+                if (gl == 0) P->h_ctrl = h;
+                h = hp;
+                last = false;
+                proposed = true;
+            }
         }
 
         // (B): one Dormand-Prince attempt; K_6 = M ynew
@@ -492,7 +628,7 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
                 b = L.xnext();
                 dense_rows<Ar, G, R>(C, L, h, thj, b);
                 g.sync();
-                record_outputs<Ar, G, R>(a, g, si, sv, b, j, out);
+                record_outputs<Ar, G, R>(a, g, si, sv, b, j, out, obs);
             }
             b = L.xnext();
             dense_rows<Ar, G, R>(C, L, h, th, b);
@@ -508,9 +644,14 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
             }
             ++n_jump;
 
+            if constexpr (PROP)
+                if (proposed) h = P->h_ctrl;  // a proposed step was shortened on purpose
+
             // (D)
             ++k;
             jump_draws(a.seed, traj, k, rk, ck);
+            if constexpr (PROP)
+                if (gl == 0) prop_jumped(a, P, il, tau, rk);
             t = tau;
             b = L.xnext();
 #pragma unroll
@@ -531,13 +672,20 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
             b = L.xnext();
             dense_rows<Ar, G, R>(C, L, h, thj, b);
             g.sync();
-            record_outputs<Ar, G, R>(a, g, si, sv, b, j, out);
+            record_outputs<Ar, G, R>(a, g, si, sv, b, j, out, obs);
         }
         double fac = (err == 0.0) ? kFacMax : Ar::controller(err);
         if (fac > kFacMax) fac = kFacMax;
         if (fac < kFacMin) fac = kFacMin;
         if (rejected_before && fac > 1.0) fac = 1.0;
         rejected_before = false;
+        if constexpr (PROP) {
+            if (gl == 0) prop_accepted(P, nn, t, h);
+            if (proposed) {
+                if (fac < 1.0) fac = 1.0;  // a shortened step says nothing about accuracy
+                h = P->h_ctrl / fac;       // resume the controller's own step size below
+            }
+        }
         t = t_new;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -578,7 +726,7 @@ __host__ __device__ constexpr int block_for_group() { return G <= 32 ? 128 : 256
 template <int G>
 __host__ __device__ constexpr bool ops_in_shared() { return G <= 32; }
 
-template <class Ar, int G, int R, int BLOCK>
+template <class Ar, int G, int R, int BLOCK, bool PROP>
 __global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 1)) mcwf_kernel(const __grid_constant__ KernelArgs a)
 {
     using cplx = typename Ar::cplx;
@@ -612,17 +760,20 @@ __global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 1)) mcwf_kernel(const __
     const Group<G> g(threadIdx.x, reinterpret_cast<unsigned long long *>(smem + a.smem_scratch_offset));
     Lanes<Ar, G, R> L{reinterpret_cast<cplx *>(smem + a.smem_ybuf_offset) + (threadIdx.x / G) * kNumSlots * (G * R),
                       g.gl, a.n, 0};
+    unsigned char *pbase = smem + a.smem_mlp_offset + (size_t)(threadIdx.x / G) * kPropStride;
+    float *hscratch = PROP ? reinterpret_cast<float *>(pbase) : nullptr;
+    PropState *P = PROP ? reinterpret_cast<PropState *>(pbase + kMlpHidden * sizeof(float)) : nullptr;
     for (;;) {
         unsigned long long i = 0;
         if (g.gl == 0) i = atomicAdd(a.queue, 1ULL);
         i = g.bcast0(i);
         if ((long long)i >= a.ntraj) break;
-        run_trajectory<Ar, G, R>(a, g, si, sv, *C, L, (long long)i);
+        run_trajectory<Ar, G, R, PROP>(a, g, si, sv, *C, L, hscratch, P, (long long)i);
     }
 }
 
 // Shared-memory layout and occupancy-sized persistent launch of one instantiation.
-template <class Ar, int G, int R>
+template <class Ar, int G, int R, bool PROP = false>
 cudaError_t launch_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInfo *info)
 {
     using cplx = typename Ar::cplx;
@@ -634,13 +785,15 @@ cudaError_t launch_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInf
     const size_t vb = ops_in_shared<G>() ? al16((size_t)a.n_vals * sizeof(typename Ar::real)) : 0;
     const size_t cb = al16(sizeof(Coefs<Ar>));
     const size_t sb = al16((size_t)GROUPS * (Group<G>::kWarps + 1) * 8);
+    const size_t mb = PROP ? (size_t)GROUPS * kPropStride : 0;
     a.smem_vals_offset = (int)ib;
     a.smem_coef_offset = (int)(ib + vb);
     a.smem_scratch_offset = (int)(ib + vb + cb);
-    a.smem_ybuf_offset = (int)(ib + vb + cb + sb);
-    const size_t smem = ib + vb + cb + sb + (size_t)GROUPS * kNumSlots * G * R * sizeof(cplx);
+    a.smem_mlp_offset = (int)(ib + vb + cb + sb);
+    a.smem_ybuf_offset = (int)(ib + vb + cb + sb + mb);
+    const size_t smem = ib + vb + cb + sb + mb + (size_t)GROUPS * kNumSlots * G * R * sizeof(cplx);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    auto kern = mcwf_kernel<Ar, G, R, BLOCK>;
+    auto kern = mcwf_kernel<Ar, G, R, BLOCK, PROP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // the trajectory state lives in shared memory: ask for the largest carveout
@@ -668,18 +821,18 @@ cudaError_t launch_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInf
 // The instantiation for the layout the operators were packed with (a.G, a.R):
 // single-warp groups here, multi-warp groups in launch_large.  The layouts are
 // those of layout_candidates.
-template <class Ar>
+template <class Ar, bool PROP = false>
 cudaError_t launch_small(const KernelArgs &a, cudaStream_t stream, LaunchInfo *info)
 {
-    if (a.G == 1 && a.R == 2) return launch_instance<Ar, 1, 2>(a, stream, info);
-    if (a.G == 4 && a.R == 2) return launch_instance<Ar, 4, 2>(a, stream, info);
-    if (a.G == 4 && a.R == 4) return launch_instance<Ar, 4, 4>(a, stream, info);
-    if (a.G == 8 && a.R == 2) return launch_instance<Ar, 8, 2>(a, stream, info);
-    if (a.G == 8 && a.R == 4) return launch_instance<Ar, 8, 4>(a, stream, info);
-    if (a.G == 16 && a.R == 2) return launch_instance<Ar, 16, 2>(a, stream, info);
-    if (a.G == 16 && a.R == 4) return launch_instance<Ar, 16, 4>(a, stream, info);
-    if (a.G == 32 && a.R == 2) return launch_instance<Ar, 32, 2>(a, stream, info);
-    if (a.G == 32 && a.R == 4) return launch_instance<Ar, 32, 4>(a, stream, info);
+    if (a.G == 1 && a.R == 2) return launch_instance<Ar, 1, 2, PROP>(a, stream, info);
+    if (a.G == 4 && a.R == 2) return launch_instance<Ar, 4, 2, PROP>(a, stream, info);
+    if (a.G == 4 && a.R == 4) return launch_instance<Ar, 4, 4, PROP>(a, stream, info);
+    if (a.G == 8 && a.R == 2) return launch_instance<Ar, 8, 2, PROP>(a, stream, info);
+    if (a.G == 8 && a.R == 4) return launch_instance<Ar, 8, 4, PROP>(a, stream, info);
+    if (a.G == 16 && a.R == 2) return launch_instance<Ar, 16, 2, PROP>(a, stream, info);
+    if (a.G == 16 && a.R == 4) return launch_instance<Ar, 16, 4, PROP>(a, stream, info);
+    if (a.G == 32 && a.R == 2) return launch_instance<Ar, 32, 2, PROP>(a, stream, info);
+    if (a.G == 32 && a.R == 4) return launch_instance<Ar, 32, 4, PROP>(a, stream, info);
     return cudaErrorInvalidValue;
 }
 

@@ -8,6 +8,7 @@
 // reduction on the context's stream; the synchronising calls copy results back.
 // No numerical step of a trajectory runs on the host.
 
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -19,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/qtm.h"
+#include "proposal.cuh"
 #include "qtm_launch.h"
 
 using cd = std::complex<double>;
@@ -67,6 +69,12 @@ struct qtm_ctx {
     std::vector<Csr> Cops, Aops;
     DevBuf d_ints, d_vals, d_t, d_psi0, d_queue, d_counters, d_first_error;
     DevBuf d_out, d_partial, d_stats, d_njumps, d_jump_t, d_jump_ch;
+    // learned jump-time proposal
+    DevBuf d_rec, d_mlp, d_X, d_T, d_gpart, d_lpart, d_grad, d_loss, d_m, d_v;
+    int rec_stride = 0, rec_max = 0;
+    bool mlp_on = false, mlp_set = false;
+    float prop_margin = 0.05f;
+    std::vector<float> pair_f, pair_dt;  // collected (raw features, time left to the jump)
     qtm::Layout layout{0, 0};
     long long last_ntraj = -1;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // kernel start, kernel end, reduction end
@@ -362,7 +370,9 @@ void destroy_ctx(qtm_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     DevBuf *bufs[] = {&ctx->d_ints, &ctx->d_vals, &ctx->d_t, &ctx->d_psi0, &ctx->d_queue,
                       &ctx->d_counters, &ctx->d_first_error, &ctx->d_out, &ctx->d_partial,
-                      &ctx->d_stats, &ctx->d_njumps, &ctx->d_jump_t, &ctx->d_jump_ch};
+                      &ctx->d_stats, &ctx->d_njumps, &ctx->d_jump_t, &ctx->d_jump_ch,
+                      &ctx->d_rec, &ctx->d_mlp, &ctx->d_X, &ctx->d_T, &ctx->d_gpart, &ctx->d_lpart,
+                      &ctx->d_grad, &ctx->d_loss, &ctx->d_m, &ctx->d_v};
     for (DevBuf *b : bufs) dev_free(ctx, *b);
     cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t &e : ctx->ev)
@@ -615,12 +625,21 @@ static qtm_status enqueue_run(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64
         a.n_jumps = (int *)ctx->d_njumps.p;
         a.jump_t = (double *)ctx->d_jump_t.p;
         a.jump_ch = (int *)ctx->d_jump_ch.p;
+        a.rec_stride = ctx->rec_stride;
+        a.rec_max = ctx->rec_max;
+        a.rec = (float *)ctx->d_rec.p;
+        a.mlp = ctx->mlp_on ? (const float *)ctx->d_mlp.p : nullptr;
+        a.prop_margin = ctx->prop_margin;
+        const bool prop = a.rec_stride > 0 || a.mlp != nullptr;
+        if (prop && (ctx->precision == QTM_PREC_C64 || ctx->layout.G > 32))
+            return fail(ctx, QTM_ERR_UNSUPPORTED,
+                        "qtm_run: the learned proposal needs complex128 or double-float and dimension <= 64");
         if (ctx->precision == QTM_PREC_DF64)
-            e = qtm::launch_mcwf_df64(a, s, &ctx->info);
+            e = prop ? qtm::launch_mcwf_df64_prop(a, s, &ctx->info) : qtm::launch_mcwf_df64(a, s, &ctx->info);
         else if (ctx->precision == QTM_PREC_C64)
             e = qtm::launch_mcwf_c64(a, s, &ctx->info);
         else
-            e = qtm::launch_mcwf_c128(a, s, &ctx->info);
+            e = prop ? qtm::launch_mcwf_c128_prop(a, s, &ctx->info) : qtm::launch_mcwf_c128(a, s, &ctx->info);
         if (e == cudaErrorInvalidValue)
             return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_run: no trajectory kernel fits this problem");
         if (e != cudaSuccess) return cuda_fail(ctx, e, "qtm_run: trajectory kernel launch");
@@ -942,6 +961,245 @@ qtm_status qtm_stats(qtm_ctx *ctx, qtm_stats_t *out)
         if (cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]) == cudaSuccess) out->reduce_ms = ms;
     }
     return QTM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// learned jump-time proposal
+// ---------------------------------------------------------------------------
+
+namespace {
+// splitmix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014): deterministic initialisation and shuffling
+uint64_t splitmix64(uint64_t &x)
+{
+    uint64_t z = (x += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+double uniform01(uint64_t &x) { return (double)(splitmix64(x) >> 11) * 0x1.0p-53; }
+
+// constant-rate estimate of the time left: log(<psi|psi> / r) / Gamma
+double rate_estimate(const float *f) { return (std::log((double)f[2]) - (double)f[3]) / (double)f[0]; }
+
+// The proposal is compiled into the complex128 and double-float kernels of the
+// single-warp lane layouts only.
+bool proposal_supported(const qtm_ctx *ctx)
+{
+    return ctx->precision != QTM_PREC_C64 && ctx->layout.G <= 32;
+}
+}  // namespace
+
+qtm_status qtm_proposal_collect(qtm_ctx *ctx, int64_t ntraj, uint64_t seed, int32_t stride, int32_t max_per_traj,
+                                int64_t *npairs)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_proposal_collect: ctx is NULL");
+    ctx->err.clear();
+    if (ntraj < 1 || stride < 1 || max_per_traj < 1 || ntraj > ((int64_t)1 << 32))
+        return fail(ctx, QTM_ERR_ARG, "qtm_proposal_collect: need ntraj, stride, max_per_traj >= 1");
+    if (!proposal_supported(ctx))
+        return fail(ctx, QTM_ERR_UNSUPPORTED,
+                    "qtm_proposal_collect: the proposal needs complex128 or double-float and dimension <= 64");
+    qtm_status st = reserve_run(ctx, ntraj);
+    if (st) return st;
+    const size_t rec_floats = (size_t)ntraj * max_per_traj * qtm::kRecFloats;
+    cudaError_t e;
+    if ((e = dev_reserve(ctx, ctx->d_rec, rec_floats * sizeof(float))) ||
+        (e = cudaMemsetAsync(ctx->d_rec.p, 0xff, rec_floats * sizeof(float), ctx->stream)))
+        return cuda_fail(ctx, e, "qtm_proposal_collect: record buffer");
+    const bool was_on = ctx->mlp_on;
+    ctx->mlp_on = false;  // pairs come from the plain method
+    ctx->rec_stride = stride;
+    ctx->rec_max = max_per_traj;
+    st = enqueue_run(ctx, 0, ntraj, seed, ctx->stream, true);
+    ctx->rec_stride = 0;
+    ctx->mlp_on = was_on;
+    if (st) return st;
+    ctx->timed = true;
+    ctx->last_ntraj = ntraj;
+    std::vector<float> rec(rec_floats);
+    if ((e = cudaMemcpyAsync(rec.data(), ctx->d_rec.p, rec_floats * sizeof(float), cudaMemcpyDeviceToHost,
+                             ctx->stream)) ||
+        (e = cudaStreamSynchronize(ctx->stream)))
+        return cuda_fail(ctx, e, "qtm_proposal_collect: copy");
+    ctx->pair_f.clear();
+    ctx->pair_dt.clear();
+    for (size_t q = 0; q < rec.size() / qtm::kRecFloats; ++q) {
+        const float *r = &rec[q * qtm::kRecFloats];
+        // a complete record: positive rate, a jump that followed, a finite estimate
+        if (!(r[0] > 0.f) || !(r[7] > 0.f) || !std::isfinite(r[7])) continue;
+        const double est = rate_estimate(r);
+        if (!(est > 0.0) || !std::isfinite(est)) continue;
+        ctx->pair_f.insert(ctx->pair_f.end(), r, r + qtm::kMlpIn);
+        ctx->pair_dt.push_back(r[7]);
+    }
+    if (npairs) *npairs = (int64_t)ctx->pair_dt.size();
+    return QTM_OK;
+}
+
+qtm_status qtm_proposal_pairs(qtm_ctx *ctx, float *features, float *dt, int64_t capacity)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_proposal_pairs: ctx is NULL");
+    if (!features || !dt) return fail(ctx, QTM_ERR_ARG, "qtm_proposal_pairs: NULL output");
+    const int64_t n = std::min<int64_t>(capacity, (int64_t)ctx->pair_dt.size());
+    std::memcpy(features, ctx->pair_f.data(), (size_t)n * qtm::kMlpIn * sizeof(float));
+    std::memcpy(dt, ctx->pair_dt.data(), (size_t)n * sizeof(float));
+    return QTM_OK;
+}
+
+qtm_status qtm_proposal_train(qtm_ctx *ctx, int32_t steps, int32_t batch, float lr, uint64_t seed, float *loss,
+                              float *loss_rate_estimate)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_proposal_train: ctx is NULL");
+    ctx->err.clear();
+    const int64_t np = (int64_t)ctx->pair_dt.size();
+    if (np < 64) return fail(ctx, QTM_ERR_STATE, "qtm_proposal_train: collect at least 64 pairs first");
+    if (steps < 1 || batch < 1 || !(lr > 0.f)) return fail(ctx, QTM_ERR_ARG, "qtm_proposal_train: bad settings");
+    if (batch > np) batch = (int32_t)np;
+    // feature normalisation and targets: y = log(true time left / constant-rate estimate)
+    double mu[qtm::kMlpIn] = {0}, sd[qtm::kMlpIn] = {0};
+    for (int64_t i = 0; i < np; ++i)
+        for (int k = 0; k < qtm::kMlpIn; ++k) mu[k] += ctx->pair_f[i * qtm::kMlpIn + k];
+    for (double &m : mu) m /= (double)np;
+    for (int64_t i = 0; i < np; ++i)
+        for (int k = 0; k < qtm::kMlpIn; ++k) {
+            const double d = ctx->pair_f[i * qtm::kMlpIn + k] - mu[k];
+            sd[k] += d * d;
+        }
+    for (double &s : sd) s = std::sqrt(s / (double)np) + 1e-12;
+    std::vector<int64_t> order(np);
+    for (int64_t i = 0; i < np; ++i) order[i] = i;
+    uint64_t rng = seed ^ 0x5DEECE66DULL;
+    for (int64_t i = np - 1; i > 0; --i) std::swap(order[i], order[(int64_t)(uniform01(rng) * (double)(i + 1))]);
+    std::vector<float> X((size_t)np * qtm::kMlpIn), T((size_t)np);
+    double base = 0.0;
+    for (int64_t i = 0; i < np; ++i) {
+        const float *f = &ctx->pair_f[order[i] * qtm::kMlpIn];
+        for (int k = 0; k < qtm::kMlpIn; ++k) X[i * qtm::kMlpIn + k] = (float)((f[k] - mu[k]) / sd[k]);
+        T[i] = (float)std::log((double)ctx->pair_dt[order[i]] / rate_estimate(f));
+        base += (double)T[i] * T[i];
+    }
+    // Glorot-uniform weights, zero biases
+    std::vector<float> P(qtm::kMlpBlock, 0.f);
+    auto glorot = [&](int off, int fan_out, int fan_in) {
+        const double a = std::sqrt(6.0 / (fan_in + fan_out));
+        for (int i = 0; i < fan_out * fan_in; ++i) P[off + i] = (float)((2.0 * uniform01(rng) - 1.0) * a);
+    };
+    glorot(qtm::kOffW1, qtm::kMlpHidden, qtm::kMlpIn);
+    glorot(qtm::kOffW2, qtm::kMlpHidden, qtm::kMlpHidden);
+    glorot(qtm::kOffW3, 1, qtm::kMlpHidden);
+    for (int k = 0; k < qtm::kMlpIn; ++k) {
+        P[qtm::kOffMu + k] = (float)mu[k];
+        P[qtm::kOffSd + k] = (float)sd[k];
+    }
+    const int tiles = qtm::mlp_tile_count(batch);
+    cudaError_t e;
+    if ((e = dev_reserve(ctx, ctx->d_mlp, qtm::kMlpBlock * sizeof(float))) ||
+        (e = dev_reserve(ctx, ctx->d_X, X.size() * sizeof(float))) ||
+        (e = dev_reserve(ctx, ctx->d_T, T.size() * sizeof(float))) ||
+        (e = dev_reserve(ctx, ctx->d_gpart, (size_t)tiles * qtm::kMlpParams * sizeof(float))) ||
+        (e = dev_reserve(ctx, ctx->d_lpart, (size_t)tiles * sizeof(float))) ||
+        (e = dev_reserve(ctx, ctx->d_grad, qtm::kMlpParams * sizeof(float))) ||
+        (e = dev_reserve(ctx, ctx->d_loss, 16)) ||
+        (e = dev_reserve(ctx, ctx->d_m, qtm::kMlpParams * sizeof(float))) ||
+        (e = dev_reserve(ctx, ctx->d_v, qtm::kMlpParams * sizeof(float))))
+        return cuda_fail(ctx, e, "qtm_proposal_train: device allocation");
+    if ((e = cudaMemcpyAsync(ctx->d_mlp.p, P.data(), P.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream)) ||
+        (e = cudaMemcpyAsync(ctx->d_X.p, X.data(), X.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream)) ||
+        (e = cudaMemcpyAsync(ctx->d_T.p, T.data(), T.size() * sizeof(float), cudaMemcpyHostToDevice, ctx->stream)) ||
+        (e = cudaMemsetAsync(ctx->d_m.p, 0, qtm::kMlpParams * sizeof(float), ctx->stream)) ||
+        (e = cudaMemsetAsync(ctx->d_v.p, 0, qtm::kMlpParams * sizeof(float), ctx->stream)))
+        return cuda_fail(ctx, e, "qtm_proposal_train: upload");
+    float *dP = (float *)ctx->d_mlp.p, *dX = (float *)ctx->d_X.p, *dT = (float *)ctx->d_T.p;
+    for (int s = 0; s < steps; ++s) {
+        int64_t off = ((int64_t)s * batch) % np;
+        if (off + batch > np) off = 0;
+        if ((e = qtm::mlp_loss_grad(dP, dX + off * qtm::kMlpIn, dT + off, batch, (float *)ctx->d_gpart.p,
+                                    (float *)ctx->d_lpart.p, (float *)ctx->d_grad.p, (float *)ctx->d_loss.p,
+                                    ctx->stream)) ||
+            (e = qtm::mlp_adam_step(dP, (float *)ctx->d_m.p, (float *)ctx->d_v.p, (const float *)ctx->d_grad.p, lr,
+                                    s + 1, ctx->stream)))
+            return cuda_fail(ctx, e, "qtm_proposal_train: training kernels");
+    }
+    // final loss over every pair (network forward pass on the GPU)
+    DevBuf dY;
+    if ((e = dev_alloc(ctx, dY, (size_t)np * sizeof(float))) ||
+        (e = qtm::mlp_forward(dP, dX, np, (float *)dY.p, ctx->stream)))
+        return cuda_fail(ctx, e, "qtm_proposal_train: evaluation");
+    std::vector<float> Y((size_t)np);
+    e = cudaMemcpyAsync(Y.data(), dY.p, Y.size() * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream);
+    if (!e) e = cudaStreamSynchronize(ctx->stream);
+    dev_free(ctx, dY);
+    if (e) return cuda_fail(ctx, e, "qtm_proposal_train: evaluation");
+    double l = 0.0;
+    for (int64_t i = 0; i < np; ++i) l += ((double)Y[i] - T[i]) * ((double)Y[i] - T[i]);
+    if (loss) *loss = (float)(l / (double)np);
+    if (loss_rate_estimate) *loss_rate_estimate = (float)(base / (double)np);
+    ctx->mlp_set = true;
+    return QTM_OK;
+}
+
+qtm_status qtm_proposal_set(qtm_ctx *ctx, const float *params)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_proposal_set: ctx is NULL");
+    if (!params) return fail(ctx, QTM_ERR_ARG, "qtm_proposal_set: params is NULL");
+    for (int k = 0; k < qtm::kMlpIn; ++k)
+        if (!(params[qtm::kOffSd + k] > 0.f)) return fail(ctx, QTM_ERR_ARG, "qtm_proposal_set: feature scales must be > 0");
+    cudaError_t e;
+    if ((e = dev_reserve(ctx, ctx->d_mlp, qtm::kMlpBlock * sizeof(float))) ||
+        (e = cudaMemcpyAsync(ctx->d_mlp.p, params, qtm::kMlpBlock * sizeof(float), cudaMemcpyHostToDevice,
+                             ctx->stream)) ||
+        (e = cudaStreamSynchronize(ctx->stream)))
+        return cuda_fail(ctx, e, "qtm_proposal_set: upload");
+    ctx->mlp_set = true;
+    return QTM_OK;
+}
+
+qtm_status qtm_proposal_get(qtm_ctx *ctx, float *params)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_proposal_get: ctx is NULL");
+    if (!params) return fail(ctx, QTM_ERR_ARG, "qtm_proposal_get: params is NULL");
+    if (!ctx->mlp_set) return fail(ctx, QTM_ERR_STATE, "qtm_proposal_get: no network trained or set");
+    cudaError_t e = cudaMemcpyAsync(params, ctx->d_mlp.p, qtm::kMlpBlock * sizeof(float), cudaMemcpyDeviceToHost,
+                                    ctx->stream);
+    if (!e) e = cudaStreamSynchronize(ctx->stream);
+    return e ? cuda_fail(ctx, e, "qtm_proposal_get: copy") : QTM_OK;
+}
+
+qtm_status qtm_proposal_enable(qtm_ctx *ctx, int32_t on, float margin)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_proposal_enable: ctx is NULL");
+    if (on && !ctx->mlp_set) return fail(ctx, QTM_ERR_STATE, "qtm_proposal_enable: no network trained or set");
+    if (!(margin > 0.f) || !(margin < 1.f)) return fail(ctx, QTM_ERR_ARG, "qtm_proposal_enable: margin in (0, 1)");
+    if (on && !proposal_supported(ctx))
+        return fail(ctx, QTM_ERR_UNSUPPORTED,
+                    "qtm_proposal_enable: the proposal needs complex128 or double-float and dimension <= 64");
+    ctx->mlp_on = on != 0;
+    ctx->prop_margin = margin;
+    return QTM_OK;
+}
+
+qtm_status qtm_mlp_loss_grad(const float *params, const float *x, const float *t, int64_t n, float *loss,
+                             float *grad)
+{
+    if (!params || !x || !t || !loss || !grad || n < 1)
+        return fail(nullptr, QTM_ERR_ARG, "qtm_mlp_loss_grad: NULL buffer or n < 1");
+    const int tiles = qtm::mlp_tile_count(n);
+    float *d = nullptr;
+    const size_t nf = qtm::kMlpParams + (size_t)n * (qtm::kMlpIn + 1) + (size_t)tiles * (qtm::kMlpParams + 1) +
+                      qtm::kMlpParams + 1;
+    cudaError_t e = cudaMalloc(&d, nf * sizeof(float));
+    if (e) return cuda_fail(nullptr, e, "qtm_mlp_loss_grad: cudaMalloc");
+    float *dP = d, *dX = dP + qtm::kMlpParams, *dT = dX + n * qtm::kMlpIn, *dG = dT + n;
+    float *dL = dG + (size_t)tiles * qtm::kMlpParams, *dgrad = dL + tiles, *dloss = dgrad + qtm::kMlpParams;
+    if (!(e = cudaMemcpy(dP, params, qtm::kMlpParams * sizeof(float), cudaMemcpyHostToDevice)) &&
+        !(e = cudaMemcpy(dX, x, (size_t)n * qtm::kMlpIn * sizeof(float), cudaMemcpyHostToDevice)) &&
+        !(e = cudaMemcpy(dT, t, (size_t)n * sizeof(float), cudaMemcpyHostToDevice)) &&
+        !(e = qtm::mlp_loss_grad(dP, dX, dT, n, dG, dL, dgrad, dloss, nullptr)) &&
+        !(e = cudaMemcpy(grad, dgrad, qtm::kMlpParams * sizeof(float), cudaMemcpyDeviceToHost)))
+        e = cudaMemcpy(loss, dloss, sizeof(float), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    return e ? cuda_fail(nullptr, e, "qtm_mlp_loss_grad") : QTM_OK;
 }
 
 void qtm_destroy(qtm_ctx *ctx) { destroy_ctx(ctx); }

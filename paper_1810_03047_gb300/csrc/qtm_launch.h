@@ -87,6 +87,13 @@ struct KernelArgs {
     int smem_vals_offset;     // byte offset of the value array in dynamic shared memory
     int smem_coef_offset;     // byte offset of the method's coefficient tables
     int smem_scratch_offset;  // byte offset of the multi-warp groups' reduction scratch
+    int smem_mlp_offset;      // byte offset of the proposal network's per-group scratch
+    // learned jump-time proposal
+    int rec_stride;           // > 0: record a training pair every rec_stride accepted steps
+    int rec_max;              // records per trajectory
+    float *rec;               // [ntraj][rec_max][8]: 6 features, time, time left to the next jump
+    const float *mlp;         // proposal network (weights and feature normalisation) or null
+    float prop_margin;        // a proposed step ends this fraction past the predicted crossing
     int smem_ybuf_offset;     // byte offset of the per-trajectory vector slots
 };
 
@@ -111,6 +118,9 @@ cudaError_t launch_mcwf_df64_small(const KernelArgs &args, cudaStream_t stream, 
 cudaError_t launch_mcwf_df64_large(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
 cudaError_t launch_mcwf_c64_small(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
 cudaError_t launch_mcwf_c64_large(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+// Instantiations with the learned proposal compiled in (single-warp layouts only).
+cudaError_t launch_mcwf_c128_prop(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+cudaError_t launch_mcwf_df64_prop(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
 inline cudaError_t launch_mcwf_c128(const KernelArgs &a, cudaStream_t s, LaunchInfo *i)
 {
     return a.G <= 32 ? launch_mcwf_c128_small(a, s, i) : launch_mcwf_c128_large(a, s, i);

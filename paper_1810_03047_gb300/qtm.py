@@ -41,7 +41,11 @@ EXPORTS = ["qtm_set_allocator", "qtm_create", "qtm_run", "qtm_run_range", "qtm_e
            "qtm_sums_device",
            "qtm_traj_expect", "qtm_jumps", "qtm_stats", "qtm_last_error", "qtm_status_string",
            "qtm_destroy", "qtm_version", "qtm_ensemble_reduce_static", "qtm_run_batch", "qtm_autotune",
-           "qtm_set_layout"]
+           "qtm_set_layout", "qtm_proposal_collect", "qtm_proposal_pairs", "qtm_proposal_train",
+           "qtm_proposal_set", "qtm_proposal_get", "qtm_proposal_enable", "qtm_mlp_loss_grad"]
+
+QTM_PROPOSAL_FLOATS = 4685
+MLP_PARAMS = 4673
 
 
 class QtmError(RuntimeError):
@@ -117,6 +121,18 @@ def lib():
             L.qtm_autotune.restype = ct.c_int
             L.qtm_set_layout.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32]
             L.qtm_set_layout.restype = ct.c_int
+            fp = ct.POINTER(ct.c_float)
+            L.qtm_proposal_collect.argtypes = [ct.c_void_p, ct.c_int64, ct.c_uint64, ct.c_int32, ct.c_int32,
+                                               ct.POINTER(ct.c_int64)]
+            L.qtm_proposal_pairs.argtypes = [ct.c_void_p, fp, fp, ct.c_int64]
+            L.qtm_proposal_train.argtypes = [ct.c_void_p, ct.c_int32, ct.c_int32, ct.c_float, ct.c_uint64, fp, fp]
+            L.qtm_proposal_set.argtypes = [ct.c_void_p, fp]
+            L.qtm_proposal_get.argtypes = [ct.c_void_p, fp]
+            L.qtm_proposal_enable.argtypes = [ct.c_void_p, ct.c_int32, ct.c_float]
+            L.qtm_mlp_loss_grad.argtypes = [fp, fp, fp, ct.c_int64, fp, fp]
+            for name in ("qtm_proposal_collect", "qtm_proposal_pairs", "qtm_proposal_train", "qtm_proposal_set",
+                         "qtm_proposal_get", "qtm_proposal_enable", "qtm_mlp_loss_grad"):
+                getattr(L, name).restype = ct.c_int
             for name in ("qtm_create", "qtm_run", "qtm_run_range", "qtm_expect", "qtm_sums", "qtm_sums_device",
                          "qtm_traj_expect", "qtm_jumps", "qtm_stats", "qtm_set_allocator"):
                 getattr(L, name).restype = ct.c_int
@@ -288,6 +304,62 @@ def qtm_autotune(ctx: Ctx, sample: int, seed: int = 1):
 
 def qtm_set_layout(ctx: Ctx, group: int, rows: int):
     _check(lib().qtm_set_layout(ctx.handle, int(group), int(rows)), ctx)
+
+
+def _fp(a):
+    return a.ctypes.data_as(ct.POINTER(ct.c_float))
+
+
+def qtm_proposal_collect(ctx: Ctx, ntraj: int, seed: int, stride: int = 16, max_per_traj: int = 64) -> int:
+    n = ct.c_int64()
+    _check(lib().qtm_proposal_collect(ctx.handle, int(ntraj), int(seed), int(stride), int(max_per_traj),
+                                      ct.byref(n)), ctx)
+    ctx.last_ntraj = int(ntraj)
+    return n.value
+
+
+def qtm_proposal_pairs(ctx: Ctx, capacity: int):
+    f = np.zeros((capacity, 6), np.float32)
+    dt = np.zeros(capacity, np.float32)
+    _check(lib().qtm_proposal_pairs(ctx.handle, _fp(f), _fp(dt), int(capacity)), ctx)
+    return f, dt
+
+
+def qtm_proposal_train(ctx: Ctx, steps: int = 2000, batch: int = 4096, lr: float = 2e-3, seed: int = 11):
+    """Trains the proposal network on the collected pairs; returns (loss, loss of the
+    constant-rate estimate alone)."""
+    loss = ct.c_float()
+    base = ct.c_float()
+    _check(lib().qtm_proposal_train(ctx.handle, int(steps), int(batch), float(lr), int(seed), ct.byref(loss),
+                                    ct.byref(base)), ctx)
+    return loss.value, base.value
+
+
+def qtm_proposal_set(ctx: Ctx, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == QTM_PROPOSAL_FLOATS
+    _check(lib().qtm_proposal_set(ctx.handle, _fp(p)), ctx)
+
+
+def qtm_proposal_get(ctx: Ctx):
+    p = np.zeros(QTM_PROPOSAL_FLOATS, np.float32)
+    _check(lib().qtm_proposal_get(ctx.handle, _fp(p)), ctx)
+    return p
+
+
+def qtm_proposal_enable(ctx: Ctx, on: bool = True, margin: float = 0.05):
+    _check(lib().qtm_proposal_enable(ctx.handle, int(bool(on)), float(margin)), ctx)
+
+
+def qtm_mlp_loss_grad(params, x, t):
+    """(loss, gradient) of the training kernels for standardised inputs x[n][6], targets t[n]."""
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    t = np.ascontiguousarray(t, dtype=np.float32)
+    g = np.zeros(MLP_PARAMS, np.float32)
+    loss = np.zeros(1, np.float32)
+    _check(lib().qtm_mlp_loss_grad(_fp(p), _fp(x), _fp(t), len(t), _fp(loss), _fp(g)))
+    return float(loss[0]), g
 
 
 def _dp(a):
