@@ -73,7 +73,7 @@ typedef enum {
     QTM_ERR_STEPSIZE = 5,     /* step size fell below 1e-14 max(1, |t|) */
     QTM_ERR_NONFINITE = 6,    /* a non-finite error norm (NaN/Inf state) */
     QTM_ERR_NO_CHANNEL = 7,   /* the norm fell to r but every ||C_n psi|| was 0 */
-    QTM_ERR_TIMEOUT = 8,      /* reserved: a bounded device wait gave up */
+    QTM_ERR_TIMEOUT = 8,      /* a bounded device wait of the tensor-core engine gave up */
     QTM_ERR_STATE = 9,        /* call out of order (e.g. qtm_expect before qtm_run) */
     QTM_ERR_UNSUPPORTED = 10  /* the problem has no kernel in this build (e.g. dim too large) */
 } qtm_status;
@@ -88,10 +88,18 @@ enum {
                            products accumulated in double-float (about 48 bits); the
                            step-size control in FP32.  Faster, but a trajectory's jump
                            times move by about the FP32 rounding of its state */
-    QTM_PREC_DF64 = 3   /* double-float: every real is a pair of FP32 numbers hi + lo
+    QTM_PREC_DF64 = 3,  /* double-float: every real is a pair of FP32 numbers hi + lo
                            (about 48 significant bits) and every product and sum is
                            error-free-transformed on the FP32 pipe; matches complex128
                            to round-off while running on GB300's much wider FP32 units */
+    QTM_PREC_BF16X6 = 4 /* tensor-core engine for dense operators (dim <= 256): 128
+                           trajectories per SM advance in lock step and every stage
+                           product M Y (real 2N x 2N form) runs on the tcgen05 tensor
+                           cores with both operands split into three bf16 terms and
+                           the six products of combined order <= 2 accumulated in
+                           FP32 (as accurate as an FP32 product); state vectors FP32,
+                           outputs, norms and root find as complex64 with FP64
+                           scalars.  No learned proposal, no layout choice */
 };
 
 /* qtm_problem.flags */
@@ -327,6 +335,13 @@ const char *qtm_last_error(const qtm_ctx *ctx);
 
 /* Name of a status code, e.g. "QTM_ERR_ARG". */
 const char *qtm_status_string(qtm_status status);
+
+/* Batched right-hand side: my[v] = M y[v] with M = -i H_eff, for n_vec vectors
+ * y (HOST, [n_vec][dim] complex, interleaved (re, im) doubles; rounded to FP32)
+ * through the tensor-core engine's product (QTM_PREC_BF16X6 contexts only;
+ * QTM_ERR_UNSUPPORTED otherwise).  my: HOST, [n_vec][dim] complex.  Runs on the
+ * context stream and synchronises it; leaves the results of qtm_run untouched. */
+qtm_status qtm_rhs_batch(qtm_ctx *ctx, int64_t n_vec, const double *y, double *my);
 
 /* Releases the context's device memory (after synchronising its stream). NULL is ignored. */
 void qtm_destroy(qtm_ctx *ctx);

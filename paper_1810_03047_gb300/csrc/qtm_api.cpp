@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/qtm.h"
+#include "dense_tc.h"
 #include "proposal.cuh"
 #include "qtm_launch.h"
 
@@ -76,6 +77,12 @@ struct qtm_ctx {
     float prop_margin = 0.05f;
     std::vector<float> pair_f, pair_dt;  // collected (raw features, time left to the jump)
     qtm::Layout layout{0, 0};
+    // tensor-core engine (QTM_PREC_BF16X6): bf16 operator splits, their tensor
+    // map, the column state and per-column records
+    int np = 0, sms = 0;
+    DevBuf d_op, d_state, d_col, d_rhs, d_dense;
+    std::vector<int> dense_off;  // per operator: float2 offset of its dense copy, -1 = SELL
+    CUtensorMap op_map{};
     long long last_ntraj = -1;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // kernel start, kernel end, reduction end
     bool timed = false;
@@ -372,7 +379,8 @@ void destroy_ctx(qtm_ctx *ctx)
                       &ctx->d_counters, &ctx->d_first_error, &ctx->d_out, &ctx->d_partial,
                       &ctx->d_stats, &ctx->d_njumps, &ctx->d_jump_t, &ctx->d_jump_ch,
                       &ctx->d_rec, &ctx->d_mlp, &ctx->d_X, &ctx->d_T, &ctx->d_gpart, &ctx->d_lpart,
-                      &ctx->d_grad, &ctx->d_loss, &ctx->d_m, &ctx->d_v};
+                      &ctx->d_grad, &ctx->d_loss, &ctx->d_m, &ctx->d_v, &ctx->d_op, &ctx->d_state,
+                      &ctx->d_col, &ctx->d_rhs, &ctx->d_dense};
     for (DevBuf *b : bufs) dev_free(ctx, *b);
     cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t &e : ctx->ev)
@@ -387,6 +395,138 @@ void set_last_error(const char *msg) { g_create_error = msg; }
 }  // namespace qtm
 
 extern "C" {
+
+namespace {
+
+// bf16 with round-to-nearest-even (finite inputs)
+uint16_t bf16_rne(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+
+float bf16_value(uint16_t b)
+{
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// The tensor-core engine's operator: the real form Mr = [[Re M, -Im M], [Im M, Re M]]
+// of M (2 np x 2 np, zero-padded), row i = output, column k = input, split into
+// three bf16 terms x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1):
+// out = [x0 rows][x1 rows][x2 rows].
+std::vector<uint16_t> tc_operator(const Csr &M, int np)
+{
+    const int kd = 2 * np;
+    std::vector<double> mr((size_t)kd * kd, 0.0);
+    for (int i = 0; i < M.n; ++i)
+        for (int e = M.rp[i]; e < M.rp[i + 1]; ++e) {
+            const int k = M.ci[e];
+            const double re = M.val[e].real(), im = M.val[e].imag();
+            mr[(size_t)i * kd + k] = re;
+            mr[(size_t)i * kd + np + k] = -im;
+            mr[(size_t)(np + i) * kd + k] = im;
+            mr[(size_t)(np + i) * kd + np + k] = re;
+        }
+    std::vector<uint16_t> out(3 * mr.size());
+    for (size_t i = 0; i < mr.size(); ++i) {
+        double r = mr[i];
+        for (int q = 0; q < 3; ++q) {
+            const uint16_t b = bf16_rne((float)r);
+            out[q * mr.size() + i] = b;
+            r -= (double)bf16_value(b);
+        }
+    }
+    return out;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tensor map over the operator splits [3 kd rows][kd] bf16: boxes of 64 (one
+// 128-byte row) x 128 rows with the 128-byte swizzle the MMA descriptors expect.
+qtm_status tc_make_map(qtm_ctx *ctx)
+{
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "qtm_create: driver entry point");
+    if (q != cudaDriverEntryPointSuccess || !fn)
+        return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_create: the driver has no cuTensorMapEncodeTiled");
+    const int kd = 2 * ctx->np;
+    const cuuint64_t dims[2] = {(cuuint64_t)kd, (cuuint64_t)(3 * kd)};
+    const cuuint64_t strides[1] = {(cuuint64_t)kd * 2};
+    const cuuint32_t box[2] = {64, 128};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = ((EncodeTiledFn)fn)(&ctx->op_map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ctx->d_op.p, dims,
+                                           strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                           CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(ctx, QTM_ERR_CUDA, "qtm_create: cuTensorMapEncodeTiled failed");
+    return QTM_OK;
+}
+
+// Uploads the operator splits and builds the tensor map (QTM_PREC_BF16X6); also
+// the copies the engine's control warps use for their products (channel weights,
+// jumps, K_0 after a jump, observables): the np diagonal values of a diagonal
+// operator, a dense column-major FP32 copy [n][np] of an operator with at least
+// n^2/4 non-zeros; the others stay SELL.
+qtm_status tc_setup(qtm_ctx *ctx)
+{
+    ctx->np = qtm::tc_padded_dim(ctx->n);
+    std::vector<uint16_t> op = tc_operator(ctx->M, ctx->np);
+    std::vector<const Csr *> all{&ctx->M};
+    for (const Csr &c : ctx->Cops) all.push_back(&c);
+    for (const Csr &a : ctx->Aops) all.push_back(&a);
+    std::vector<float> dense;
+    ctx->dense_off.assign(all.size(), -1);
+    const size_t n = (size_t)ctx->n, np = (size_t)ctx->np;
+    for (size_t i = 0; i < all.size(); ++i) {
+        const Csr &m = *all[i];
+        bool diagonal = true;
+        for (int r = 0; r < m.n && diagonal; ++r)
+            for (int e = m.rp[r]; e < m.rp[r + 1]; ++e)
+                if (m.ci[e] != r) diagonal = false;
+        if (diagonal) {  // np complex values, encoded as -2 - offset
+            const size_t off = dense.size() / 2;
+            dense.resize(dense.size() + 2 * np, 0.f);
+            for (int r = 0; r < m.n; ++r)
+                for (int e = m.rp[r]; e < m.rp[r + 1]; ++e) {
+                    dense[2 * (off + r)] = (float)m.val[e].real();
+                    dense[2 * (off + r) + 1] = (float)m.val[e].imag();
+                }
+            ctx->dense_off[i] = -2 - (int)off;
+            continue;
+        }
+        if (4 * m.ci.size() < n * n) continue;
+        ctx->dense_off[i] = (int)(dense.size() / 2);
+        dense.resize(dense.size() + 2 * n * np, 0.f);
+        float *d = dense.data() + 2 * (size_t)ctx->dense_off[i];
+        for (int r = 0; r < m.n; ++r)
+            for (int e = m.rp[r]; e < m.rp[r + 1]; ++e) {
+                d[2 * ((size_t)m.ci[e] * np + r)] = (float)m.val[e].real();
+                d[2 * ((size_t)m.ci[e] * np + r) + 1] = (float)m.val[e].imag();
+            }
+    }
+    cudaError_t e;
+    if ((e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, ctx->device)) ||
+        (e = dev_alloc(ctx, ctx->d_op, op.size() * sizeof(uint16_t))) ||
+        (e = dev_alloc(ctx, ctx->d_dense, dense.size() * sizeof(float))) ||
+        (e = cudaMemcpyAsync(ctx->d_op.p, op.data(), op.size() * sizeof(uint16_t), cudaMemcpyHostToDevice,
+                             ctx->stream)) ||
+        (!dense.empty() && (e = cudaMemcpyAsync(ctx->d_dense.p, dense.data(), dense.size() * sizeof(float),
+                                                cudaMemcpyHostToDevice, ctx->stream))) ||
+        (e = cudaStreamSynchronize(ctx->stream)))
+        return cuda_fail(ctx, e, "qtm_create: tensor-core operator upload");
+    return tc_make_map(ctx);
+}
+
+}  // namespace
 
 const char *qtm_version(void) { return "0.1.0 sm_103a"; }
 
@@ -444,7 +584,8 @@ qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
     if (!(p->rtol > 0.0) || !(p->atol >= 0.0) || !is_finite(p->rtol) || !is_finite(p->atol))
         return fail(nullptr, QTM_ERR_ARG, "qtm_create: need rtol > 0 and atol >= 0");
     if (p->max_steps <= 0) return fail(nullptr, QTM_ERR_ARG, "qtm_create: max_steps must be > 0");
-    if (p->precision != QTM_PREC_C128 && p->precision != QTM_PREC_C64 && p->precision != QTM_PREC_DF64)
+    if (p->precision != QTM_PREC_C128 && p->precision != QTM_PREC_C64 && p->precision != QTM_PREC_DF64 &&
+        p->precision != QTM_PREC_BF16X6)
         return fail(nullptr, QTM_ERR_ARG, "qtm_create: unknown precision");
     if ((p->flags & ~QTM_FLAG_RECORD_JUMPS) != 0) return fail(nullptr, QTM_ERR_ARG, "qtm_create: unknown flags");
     if ((p->flags & QTM_FLAG_RECORD_JUMPS) && p->max_jumps_recorded < 1)
@@ -483,6 +624,10 @@ qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
         std::snprintf(buf, sizeof buf, "qtm_create: at most %d collapse operators", qtm::kMaxChannels);
         return fail(nullptr, QTM_ERR_UNSUPPORTED, buf);
     }
+    if (p->precision == QTM_PREC_BF16X6 && n > qtm::kTcMaxDim) {
+        std::snprintf(buf, sizeof buf, "qtm_create: the tensor-core path takes dim <= %d", qtm::kTcMaxDim);
+        return fail(nullptr, QTM_ERR_UNSUPPORTED, buf);
+    }
     if (qtm::layout_for_dim(n).G == 0) {
         std::snprintf(buf, sizeof buf, "qtm_create: dim %d exceeds the largest supported dimension %d", n,
                       qtm::kMaxDimSparse);
@@ -510,7 +655,9 @@ qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
     ctx->M = effective_matrix(H, C);
     ctx->Cops = C;
     ctx->Aops = A;
-    repack(ctx, qtm::layout_for_dim(n));
+    // the tensor-core engine's control warps use one lane per row group of 32
+    repack(ctx, p->precision == QTM_PREC_BF16X6 ? qtm::Layout{32, qtm::tc_padded_dim(n) / 32}
+                                                : qtm::layout_for_dim(n));
 
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e != cudaSuccess) {
@@ -553,6 +700,14 @@ qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
         destroy_ctx(ctx);
         return s;
     }
+    if (ctx->precision == QTM_PREC_BF16X6) {
+        qtm_status s = tc_setup(ctx);
+        if (s) {
+            g_create_error = ctx->err;
+            destroy_ctx(ctx);
+            return s;
+        }
+    }
     *out = ctx;
     return QTM_OK;
 }
@@ -567,6 +722,12 @@ static qtm_status reserve_run(qtm_ctx *ctx, int64_t ntraj)
         (e = dev_reserve(ctx, ctx->d_partial, 2 * (size_t)S * P * sizeof(double))) ||
         (e = dev_reserve(ctx, ctx->d_stats, 4 * P * sizeof(double))))
         return cuda_fail(ctx, e, "qtm_run: device allocation");
+    if (ctx->precision == QTM_PREC_BF16X6 && ntraj > 0) {
+        const size_t cols = (size_t)qtm::dense_tc_ctas(ntraj, ctx->sms) * qtm::kTcCols;
+        if ((e = dev_reserve(ctx, ctx->d_state, qtm::kNumDenseVecs * cols * 2 * ctx->np * sizeof(float))) ||
+            (e = dev_reserve(ctx, ctx->d_col, cols * sizeof(qtm::DenseCol))))
+            return cuda_fail(ctx, e, "qtm_run: device allocation");
+    }
     if (ctx->max_jumps > 0) {
         if ((e = dev_reserve(ctx, ctx->d_njumps, (size_t)ntraj * sizeof(int))) ||
             (e = dev_reserve(ctx, ctx->d_jump_t, (size_t)ntraj * ctx->max_jumps * sizeof(double))) ||
@@ -631,6 +792,23 @@ static qtm_status enqueue_run(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64
         a.mlp = ctx->mlp_on ? (const float *)ctx->d_mlp.p : nullptr;
         a.prop_margin = ctx->prop_margin;
         const bool prop = a.rec_stride > 0 || a.mlp != nullptr;
+        if (ctx->precision == QTM_PREC_BF16X6) {
+            if (prop) return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_run: no learned proposal on the tensor-core path");
+            qtm::DenseArgs d{};
+            d.k = a;
+            d.np = ctx->np;
+            d.cols = qtm::dense_tc_ctas(ntraj, ctx->sms) * qtm::kTcCols;
+            d.state = (float *)ctx->d_state.p;
+            d.col = (qtm::DenseCol *)ctx->d_col.p;
+            d.mode = qtm::kDenseRun;
+            d.dense = (const float2 *)ctx->d_dense.p;
+            for (int i = 0; i < qtm::kMaxOps; ++i)
+                d.dense_off[i] = i < (int)ctx->dense_off.size() ? ctx->dense_off[i] : -1;
+            e = qtm::launch_dense_tc(d, ctx->op_map, s, &ctx->info);
+            if (e == cudaErrorInvalidValue)
+                return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_run: no tensor-core kernel fits this problem");
+            if (e != cudaSuccess) return cuda_fail(ctx, e, "qtm_run: tensor-core kernel launch");
+        } else {
         if (prop && (ctx->precision == QTM_PREC_C64 || ctx->layout.G > 32))
             return fail(ctx, QTM_ERR_UNSUPPORTED,
                         "qtm_run: the learned proposal needs complex128 or double-float and dimension <= 64");
@@ -643,6 +821,7 @@ static qtm_status enqueue_run(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64
         if (e == cudaErrorInvalidValue)
             return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_run: no trajectory kernel fits this problem");
         if (e != cudaSuccess) return cuda_fail(ctx, e, "qtm_run: trajectory kernel launch");
+        }
     }
     if (with_events && (e = cudaEventRecord(ctx->ev[1], s)) != cudaSuccess)
         return cuda_fail(ctx, e, "qtm_run: cudaEventRecord");
@@ -779,6 +958,8 @@ qtm_status qtm_set_layout(qtm_ctx *ctx, int32_t group, int32_t rows)
 {
     if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_set_layout: ctx is NULL");
     ctx->err.clear();
+    if (ctx->precision == QTM_PREC_BF16X6)
+        return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_set_layout: the tensor-core path has one fixed layout");
     qtm::Layout cand[2];
     const int nc = qtm::layout_candidates(ctx->n, cand);
     for (int i = 0; i < nc; ++i)
@@ -797,6 +978,8 @@ qtm_status qtm_autotune(qtm_ctx *ctx, int64_t sample, uint64_t seed, int32_t *gr
     if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_autotune: ctx is NULL");
     ctx->err.clear();
     if (sample < 1 || sample > ((int64_t)1 << 40)) return fail(ctx, QTM_ERR_ARG, "qtm_autotune: sample must be >= 1");
+    if (ctx->precision == QTM_PREC_BF16X6)
+        return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_autotune: the tensor-core path has one fixed layout");
     qtm::Layout cand[2];
     const int nc = qtm::layout_candidates(ctx->n, cand);
     if (nc < 1) return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_autotune: no layout for this dimension");
@@ -986,7 +1169,7 @@ double rate_estimate(const float *f) { return (std::log((double)f[2]) - (double)
 // single-warp lane layouts only.
 bool proposal_supported(const qtm_ctx *ctx)
 {
-    return ctx->precision != QTM_PREC_C64 && ctx->layout.G <= 32;
+    return (ctx->precision == QTM_PREC_C128 || ctx->precision == QTM_PREC_DF64) && ctx->layout.G <= 32;
 }
 }  // namespace
 
@@ -1200,6 +1383,53 @@ qtm_status qtm_mlp_loss_grad(const float *params, const float *x, const float *t
         e = cudaMemcpy(loss, dloss, sizeof(float), cudaMemcpyDeviceToHost);
     cudaFree(d);
     return e ? cuda_fail(nullptr, e, "qtm_mlp_loss_grad") : QTM_OK;
+}
+
+qtm_status qtm_rhs_batch(qtm_ctx *ctx, int64_t n_vec, const double *y, double *my)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_rhs_batch: ctx is NULL");
+    ctx->err.clear();
+    if (n_vec < 0 || (n_vec > 0 && (!y || !my))) return fail(ctx, QTM_ERR_ARG, "qtm_rhs_batch: bad arguments");
+    if (ctx->precision != QTM_PREC_BF16X6)
+        return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_rhs_batch: only the tensor-core precision has a batched product");
+    if (n_vec == 0) return QTM_OK;
+    const int n = ctx->n, np = ctx->np, kd = 2 * np;
+    std::vector<float> in((size_t)n_vec * kd, 0.f), res((size_t)n_vec * kd);
+    for (int64_t v = 0; v < n_vec; ++v)
+        for (int i = 0; i < n; ++i) {
+            in[(size_t)v * kd + i] = (float)y[2 * ((size_t)v * n + i)];
+            in[(size_t)v * kd + np + i] = (float)y[2 * ((size_t)v * n + i) + 1];
+        }
+    const size_t bytes = in.size() * sizeof(float);
+    cudaError_t e;
+    if ((e = dev_reserve(ctx, ctx->d_rhs, 16 + 2 * bytes)))
+        return cuda_fail(ctx, e, "qtm_rhs_batch: device allocation");
+    int *d_status = (int *)ctx->d_rhs.p;  // this call's own status word
+    float *d_in = (float *)((char *)ctx->d_rhs.p + 16), *d_out = d_in + in.size();
+    if ((e = cudaMemcpyAsync(d_in, in.data(), bytes, cudaMemcpyHostToDevice, ctx->stream)))
+        return cuda_fail(ctx, e, "qtm_rhs_batch: upload");
+    qtm::DenseArgs d{};
+    d.k.first_error = d_status;
+    d.np = np;
+    d.mode = qtm::kDenseRhs;
+    d.rhs_in = d_in;
+    d.rhs_out = d_out;
+    d.rhs_n = n_vec;
+    if ((e = cudaMemsetAsync(d_status, 0, 16, ctx->stream)) ||
+        (e = qtm::launch_dense_tc(d, ctx->op_map, ctx->stream, nullptr)) ||
+        (e = cudaMemcpyAsync(res.data(), d_out, bytes, cudaMemcpyDeviceToHost, ctx->stream)) ||
+        (e = cudaStreamSynchronize(ctx->stream)))
+        return cuda_fail(ctx, e, "qtm_rhs_batch: product");
+    int first = 0;
+    if ((e = cudaMemcpy(&first, d_status, sizeof(int), cudaMemcpyDeviceToHost)))
+        return cuda_fail(ctx, e, "qtm_rhs_batch: status");
+    if (first) return fail(ctx, (qtm_status)first, "qtm_rhs_batch: a device wait gave up");
+    for (int64_t v = 0; v < n_vec; ++v)
+        for (int i = 0; i < n; ++i) {
+            my[2 * ((size_t)v * n + i)] = res[(size_t)v * kd + i];
+            my[2 * ((size_t)v * n + i) + 1] = res[(size_t)v * kd + np + i];
+        }
+    return QTM_OK;
 }
 
 void qtm_destroy(qtm_ctx *ctx) { destroy_ctx(ctx); }

@@ -34,6 +34,7 @@ QTM_FORMAT_CSR = 1
 QTM_PREC_C128 = 0
 QTM_PREC_C64 = 1
 QTM_PREC_DF64 = 3
+QTM_PREC_BF16X6 = 4
 QTM_FLAG_RECORD_JUMPS = 1
 
 # every entry point declared in include/qtm.h
@@ -42,7 +43,8 @@ EXPORTS = ["qtm_set_allocator", "qtm_create", "qtm_run", "qtm_run_range", "qtm_e
            "qtm_traj_expect", "qtm_jumps", "qtm_stats", "qtm_last_error", "qtm_status_string",
            "qtm_destroy", "qtm_version", "qtm_ensemble_reduce_static", "qtm_run_batch", "qtm_autotune",
            "qtm_set_layout", "qtm_proposal_collect", "qtm_proposal_pairs", "qtm_proposal_train",
-           "qtm_proposal_set", "qtm_proposal_get", "qtm_proposal_enable", "qtm_mlp_loss_grad"]
+           "qtm_proposal_set", "qtm_proposal_get", "qtm_proposal_enable", "qtm_mlp_loss_grad",
+           "qtm_rhs_batch"]
 
 QTM_PROPOSAL_FLOATS = 4685
 MLP_PARAMS = 4673
@@ -130,6 +132,9 @@ def lib():
             L.qtm_proposal_get.argtypes = [ct.c_void_p, fp]
             L.qtm_proposal_enable.argtypes = [ct.c_void_p, ct.c_int32, ct.c_float]
             L.qtm_mlp_loss_grad.argtypes = [fp, fp, fp, ct.c_int64, fp, fp]
+            dp = ct.POINTER(ct.c_double)
+            L.qtm_rhs_batch.argtypes = [ct.c_void_p, ct.c_int64, dp, dp]
+            L.qtm_rhs_batch.restype = ct.c_int
             for name in ("qtm_proposal_collect", "qtm_proposal_pairs", "qtm_proposal_train", "qtm_proposal_set",
                          "qtm_proposal_get", "qtm_proposal_enable", "qtm_mlp_loss_grad"):
                 getattr(L, name).restype = ct.c_int
@@ -422,6 +427,15 @@ def qtm_ensemble_reduce_static(values_dev: int, ntraj: int, n_values: int, sum_d
                                             ct.c_void_p(sum_dev), ct.c_void_p(sumsq_dev),
                                             ct.c_void_p(mean_dev), ct.c_void_p(stderr_dev),
                                             ct.c_void_p(stream or 0)))
+
+
+def qtm_rhs_batch(ctx: Ctx, y) -> np.ndarray:
+    """M y for a batch of vectors y [n_vec][dim] (complex) through the tensor-core product."""
+    y = np.ascontiguousarray(np.atleast_2d(y), dtype=np.complex128)
+    out = np.empty_like(y)
+    dp = ct.POINTER(ct.c_double)
+    _check(lib().qtm_rhs_batch(ctx.handle, y.shape[0], y.ctypes.data_as(dp), out.ctypes.data_as(dp)), ctx)
+    return out
 
 
 def qtm_destroy(ctx: Ctx):
