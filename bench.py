@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-dense", action="store_true",
+                    help="skip the dense tensor-core measurement (N = 256, 20,000 trajectories)")
     ap.add_argument("--no-proposal", action="store_true",
                     help="skip the learned jump-time proposal measurement (200,000 JC trajectories)")
     ap.add_argument("--no-ising", action="store_true",
@@ -226,7 +228,15 @@ def peaks():
             "df64": (fp32_instr / DF_INSTR_PER_FLOP / 1e12,
                      "FP64-class flops on the FP32 pipe: 152 SMs x 128 FP32 lanes x 2070 MHz = 40.3e12 "
                      "instr/s, 12 instructions per double-float multiply-add (2 flop)"),
-            "c64": (2 * fp32_instr / 1e12, "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz")}
+            "c64": (2 * fp32_instr / 1e12, "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz"),
+            "hbm": _hbm_peak()}
+
+
+def _hbm_peak():
+    mp = measured_peaks()
+    if "hbm_gbs" in mp:
+        return float(mp["hbm_gbs"]), "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs), of measured"
+    return 6800.0, "fallback 6.8 TB/s (one earlier GB300 measurement), of fallback"
 
 
 def main():
@@ -393,6 +403,9 @@ def main():
     if not args.no_ising:
         line["ising_batch"] = ising_batch(Q, torch, stream, world, rank, dist)
         line["gpu_launches"] += line["ising_batch"].pop("launches")
+    if not args.no_dense:
+        line["dense_tensor_core"] = dense_tensor_core(Q, torch, stream, world, rank, dist, pk)
+        line["gpu_launches"] += line["dense_tensor_core"].pop("launches")
     if not args.no_proposal:
         line["learned_proposal"] = learned_proposal(Q, torch, stream, world, rank, dist)
         line["gpu_launches"] += line["learned_proposal"].pop("launches")
@@ -447,6 +460,72 @@ def ising_batch(Q, torch, stream, world, rank, dist):
                         "one CUDA-graph launch", "precision": "df64",
             "value": world * sum(counts) / (float(t.item()) / 1e3), "unit": UNIT, "ms_per_step": float(t.item()),
             "observable_error": err, "layouts": [list(x) for x in layouts], "launches": 2 * 5 * 5}
+
+
+def dense_tensor_core(Q, torch, stream, world, rank, dist, pk, ntraj=20000, sample=2000):
+    """The dense random open system (GUE H, N = 256, four Ginibre channels with
+    ||C_n||_2 = 0.3, 101 outputs on [0, 10], observable diag(0..N-1)/N, operators
+    from default_rng(3), seed 1) through the tensor-core engine (BF16x6 stage
+    products on tcgen05, FP32 state), 20,000 trajectories per GPU: one warm-up
+    pass, two timed.  The plain FP64 GPU path (complex128) runs the first 2,000
+    trajectory ids for its throughput and for the observable error on the same
+    trajectories.  Roofline: the engine is bound by device memory -- per attempted
+    step and trajectory it reads psi and the stage vectors 26 times while forming
+    the six stage inputs, writes six stage vectors and ynew, and reads eight vectors
+    for the error estimate: 41 passes over 2N FP32 values."""
+    from paper_1810_03047_gb300 import shards
+    from paper_1810_03047_gb300 import systems as S
+    prob = S.dense_random(ntraj=ntraj)
+    sid = int(stream.cuda_stream)
+    first, count = shards.shard(world * ntraj, world, rank)
+    tc = Q.qtm_create(prob, stream=sid, precision=Q.QTM_PREC_BF16X6)
+    Q.qtm_run_range(tc, first, count, prob.seed)
+    Q.qtm_expect(tc)
+    times, kern, attempts = [], [], 0
+    for _ in range(2):
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Q.qtm_run_range(tc, first, count, prob.seed)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        st = Q.qtm_stats(tc)
+        kern.append(st["kernel_ms"])
+        attempts += st["accepted"] + st["rejected"]
+    t = torch.tensor([max(times)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    tc_traj = Q.qtm_traj_expect(tc)[:sample]
+    Q.qtm_destroy(tc)
+    ref = Q.qtm_create(prob, stream=sid, precision=Q.QTM_PREC_C128)
+    Q.qtm_run_range(ref, first, sample, prob.seed)
+    ref_traj = Q.qtm_traj_expect(ref)
+    ref_ms = Q.qtm_stats(ref)["kernel_ms"]
+    Q.qtm_destroy(ref)
+    err = float(np.abs(tc_traj.mean(axis=0) - ref_traj.mean(axis=0)).max())
+    n = prob.dim
+    bytes_per_attempt = 41 * 2 * n * 4
+    kms = sum(kern) / len(kern)
+    achieved = bytes_per_attempt * (attempts / 2) / (kms / 1e3) / 1e9
+    peak, note = pk["hbm"]
+    return {"workload": "dense random open system: GUE H (N=256), 4 Ginibre C_n (||C_n||_2=0.3), 101 outputs on "
+                        "[0,10], A = diag(0..N-1)/N, operators default_rng(3), seed 1",
+            "precision": "tensor-core BF16x6 products, FP32 state, FP64 scalars", "unit": UNIT,
+            "value": world * count / (ms / 1e3), "ms_per_step": ms, "ntraj_per_gpu": count,
+            "fp64_path": {"value": sample / (ref_ms / 1e3), "kernel_ms": ref_ms, "sample": sample},
+            "speedup_vs_fp64_path": (world * count / (ms / 1e3)) / (sample / (ref_ms / 1e3)),
+            "observable_error": err,
+            "observable_error_note": f"max |mean - complex128 mean| over the first {sample} trajectory ids",
+            "steps_per_trajectory": attempts / 2 / count,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "qtm::dense_tc_kernel<256>",
+                         "bytes_per_attempt": bytes_per_attempt, "peak_note": note, "kernel_ms": kms},
+            "launches": 3 * 5 + 5}
 
 
 def learned_proposal(Q, torch, stream, world, rank, dist, ntraj=200000):

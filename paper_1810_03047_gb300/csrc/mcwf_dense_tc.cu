@@ -214,7 +214,7 @@ __device__ void role_producer(const DenseArgs &a, Pipe &p, int s, long long tile
         }
         unsigned char *ytile = p.yt + ys * kSplits * kYTile;
         const int kg = kb * kKB + kk;
-#pragma unroll 2
+#pragma unroll 4
         for (int it = 0; it < 8; ++it) {
             const int row = 16 * pw + 2 * it + (lane >> 4);
             float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -279,13 +279,22 @@ __device__ void role_producer(const DenseArgs &a, Pipe &p, int s, long long tile
         dst = c.vec(kVK0 + slot);
     }
     const uint32_t tbase = p.tmem + ((uint32_t)(32 * quarter) << 16);
+    // 64 columns per round: four loads in flight, one wait
+    static_assert(S::HALF % 64 == 0, "epilogue rounds of 64 columns");
 #pragma unroll 1
-    for (int cc = hsel * S::HALF; cc < (hsel + 1) * S::HALF; cc += 16) {
-        float v[16];
-        tc::tmem_ld16(tbase + cc, v);
+    for (int cc = hsel * S::HALF; cc < (hsel + 1) * S::HALF; cc += 64) {
+        uint32_t v[4][16];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) tc::tmem_ld16_async(tbase + cc + 16 * b, v[b]);
+        tc::tmem_wait_ld();
         if (dst) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) st4(dst + cc + 4 * i, make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]));
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    st4(dst + cc + 16 * b + 4 * i,
+                        make_float4(__uint_as_float(v[b][4 * i]), __uint_as_float(v[b][4 * i + 1]),
+                                    __uint_as_float(v[b][4 * i + 2]), __uint_as_float(v[b][4 * i + 3])));
         }
     }
     tc::tc_fence_before();
