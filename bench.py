@@ -59,8 +59,11 @@ def parse():
                     help="skip the learned jump-time proposal measurement (200,000 JC trajectories)")
     ap.add_argument("--no-ising", action="store_true",
                     help="skip the batched Ising-chain measurement (L = 6..10 in one CUDA graph)")
-    ap.add_argument("--only", choices=["c128", "df64", "c64"], default=None,
-                    help="time one arithmetic only (profiling); no observable-error comparison")
+    ap.add_argument("--only", choices=["c128", "df64", "c64", "dense"], default=None,
+                    help="time one arithmetic only (profiling); no observable-error comparison.  'dense': the "
+                         "tensor-core engine on the dense N = 256 system with --ntraj trajectories")
+    ap.add_argument("--dense-t-end", type=float, default=10.0, help="--only dense: end of the time grid")
+    ap.add_argument("--dense-outputs", type=int, default=101, help="--only dense: number of output times")
     return ap.parse_args()
 
 
@@ -327,6 +330,38 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
+    if args.only == "dense":
+        from paper_1810_03047_gb300 import systems as S
+        dprob = S.dense_random(ntraj=args.ntraj, t_end=args.dense_t_end, n_t=args.dense_outputs)
+        ctx = Q.qtm_create(dprob, stream=int(stream.cuda_stream), precision=Q.QTM_PREC_BF16X6)
+        for _ in range(max(args.warmup, 0)):
+            Q.qtm_run_range(ctx, first, ntraj, dprob.seed)
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            Q.qtm_run_range(ctx, first, ntraj, dprob.seed)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        st = Q.qtm_stats(ctx)
+        Q.qtm_destroy(ctx)
+        clk = clocks.stop()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": world * ntraj / (max(ms) / 1e3), "unit": UNIT,
+                              "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                              "ms_per_step": max(ms), "higher_is_better": True, "scaling": "weak",
+                              "vs_baseline": None, "dtype": "bf16x6-tc/f32", "data": "synthetic",
+                              "config": {"workload": f"dense random N=256, t in [0, {args.dense_t_end}], "
+                                                     f"{args.dense_outputs} outputs", "ntraj_per_gpu": ntraj},
+                              "steps_per_trajectory": (st["accepted"] + st["rejected"]) / ntraj,
+                              "gpu_launches": 5 * (args.steps + max(args.warmup, 0)), "clocks": clk,
+                              "note": "tensor-core engine only (profiling run)"}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
     if args.only:
         only = timed(args.only, args.steps, args.warmup)
         clk = clocks.stop()
