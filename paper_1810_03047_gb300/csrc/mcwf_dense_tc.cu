@@ -55,7 +55,6 @@ template <int NP>
 struct TcShape {
     static constexpr int KD = 2 * NP;          // real dimension: GEMM K and N
     static constexpr int NKB = KD / kKB;       // k-blocks per product
-    static constexpr int R = NP / 32;          // complex rows per lane in the control warps
     static constexpr int NCHUNK = (KD + 255) / 256;  // 256-row output chunks (one MMA each)
     static constexpr int OP_ENTRY = 256 * 128;       // bytes of one ring entry: a chunk of one split
     static constexpr int HALF = KD / 2;        // epilogue columns per warp half
@@ -73,7 +72,6 @@ struct TcShape {
 };
 
 // Coefficient table layout (FP32): a[s][q] at 7 s + q, e[q] at 49 + q, W[j][m-1] at 56 + 5 j + m - 1.
-__device__ __forceinline__ float cA(const float *cf, int s, int q) { return cf[7 * s + q]; }
 __device__ __forceinline__ float cE(const float *cf, int q) { return cf[49 + q]; }
 __device__ __forceinline__ const float *cW(const float *cf) { return cf + 56; }
 
@@ -90,27 +88,24 @@ struct Ctl {
 __device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
 __device__ __forceinline__ void st4(float *p, float4 v) { *reinterpret_cast<float4 *>(p) = v; }
 
-__device__ __forceinline__ uint32_t pack_bf16x2(float lo_elem, float hi_elem)
-{
-    const __nv_bfloat162 v = __floats2bfloat162_rn(lo_elem, hi_elem);
-    return *reinterpret_cast<const uint32_t *>(&v);
-}
-
 // Three-term bf16 split of four FP32 values: t0 = bf16(y), t1 = bf16(y - t0),
-// t2 = bf16(y - t0 - t1) (the differences are exact in FP32).
+// t2 = bf16(y - t0 - t1) (the differences are exact in FP32); two values per
+// conversion.
 __device__ __forceinline__ void split4(float4 y, uint2 (&t)[kSplits])
 {
-    float r[4] = {y.x, y.y, y.z, y.w};
+    float2 a = make_float2(y.x, y.y), b = make_float2(y.z, y.w);
 #pragma unroll
     for (int q = 0; q < kSplits; ++q) {
-        float b[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            b[i] = __bfloat162float(__float2bfloat16_rn(r[i]));
-            r[i] -= b[i];
+        const __nv_bfloat162 ha = __float22bfloat162_rn(a), hb = __float22bfloat162_rn(b);
+        t[q].x = *reinterpret_cast<const uint32_t *>(&ha);
+        t[q].y = *reinterpret_cast<const uint32_t *>(&hb);
+        if (q + 1 < kSplits) {
+            const float2 fa = __bfloat1622float2(ha), fb = __bfloat1622float2(hb);
+            a.x -= fa.x;
+            a.y -= fa.y;
+            b.x -= fb.x;
+            b.y -= fb.y;
         }
-        t[q].x = pack_bf16x2(b[0], b[1]);
-        t[q].y = pack_bf16x2(b[2], b[3]);
     }
 }
 
@@ -197,6 +192,56 @@ __device__ void role_mma(const DenseArgs &a, Pipe &p)
     tc::mma_commit(p.acc_full);
 }
 
+// The eight rows of one k-block a producer thread forms for stage SS (0: the
+// rhs-mode input): Y_s = psi + h sum_{q<s} a_sq K_q from device memory (the
+// coefficients are compile-time constants, so only the K_q with a_sq != 0 are
+// read, all loads issued before the combination), split into three bf16 terms
+// and stored into the swizzled tiles.
+template <int NP, int SS>
+__device__ __forceinline__ void produce_rows(const DenseArgs &a, long long tile_base, int pw, int lane, int kg,
+                                             const float *s_hf, const int *s_sel, unsigned char *ytile)
+{
+    constexpr int KD = 2 * NP;
+    const int chunk = ((lane & 15) * 4) >> 3, half8 = ((lane & 15) * 4) & 7;
+    const size_t vs = (size_t)a.cols * KD;  // distance between the vectors of a column
+#pragma unroll 4
+    for (int it = 0; it < 8; ++it) {
+        const int row = 16 * pw + 2 * it + (lane >> 4);
+        float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (SS == 0) {
+            const long long g = tile_base + row;
+            if (g < a.rhs_n) y = ld4(a.rhs_in + g * KD + kg);
+        } else {
+            const float hf = s_hf[row];
+            if (hf != 0.f) {
+                const int sel = s_sel[row];
+                float *base = a.state + (size_t)(tile_base + row) * KD + kg;
+                y = ld4(base + (sel & 1) * vs);
+                float4 kv[SS];
+                kv[0] = ld4(base + (kVK0 + ((sel & 2) ? 6 : 0)) * vs);
+#pragma unroll
+                for (int q = 1; q < SS; ++q)
+                    if (DP5::a(SS, q) != 0.0) kv[q] = ld4(base + (kVK0 + q) * vs);
+#pragma unroll
+                for (int q = 0; q < SS; ++q)
+                    if (DP5::a(SS, q) != 0.0) {
+                        const float w = hf * (float)DP5::a(SS, q);
+                        y.x = fmaf(w, kv[q].x, y.x);
+                        y.y = fmaf(w, kv[q].y, y.y);
+                        y.z = fmaf(w, kv[q].z, y.z);
+                        y.w = fmaf(w, kv[q].w, y.w);
+                    }
+                if constexpr (SS == 6) st4(base + (1 - (sel & 1)) * vs, y);  // the candidate ynew
+            }
+        }
+        uint2 t[kSplits];
+        split4(y, t);
+        const int off = row * 128 + ((chunk ^ (row & 7)) << 4) + half8 * 2;
+#pragma unroll
+        for (int q = 0; q < kSplits; ++q) *reinterpret_cast<uint2 *>(ytile + q * kYTile + off) = t[q];
+    }
+}
+
 // Producer warps: k-blocks of Y_s for the tile, then the epilogue K_s <- D.
 template <int NP>
 __device__ void role_producer(const DenseArgs &a, Pipe &p, int s, long long tile_base, int pw, int lane,
@@ -205,7 +250,6 @@ __device__ void role_producer(const DenseArgs &a, Pipe &p, int s, long long tile
     using S = TcShape<NP>;
     const bool rhs = a.mode == kDenseRhs;
     const int kk = (lane & 15) * 4;  // this thread's 4 values within the 64-wide k-block
-    const int chunk = kk >> 3, half8 = kk & 7;
     for (int kb = 0; kb < S::NKB; ++kb) {
         const uint32_t ys = p.ycnt & 1, yph = (p.ycnt >> 1) & 1;
         if (!tc::mbar_wait(&p.y_empty[ys], yph ^ 1, p.abort)) {
@@ -214,43 +258,14 @@ __device__ void role_producer(const DenseArgs &a, Pipe &p, int s, long long tile
         }
         unsigned char *ytile = p.yt + ys * kSplits * kYTile;
         const int kg = kb * kKB + kk;
-#pragma unroll 4
-        for (int it = 0; it < 8; ++it) {
-            const int row = 16 * pw + 2 * it + (lane >> 4);
-            float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (rhs) {
-                const long long g = tile_base + row;
-                if (g < a.rhs_n) y = ld4(a.rhs_in + g * S::KD + kg);
-            } else {
-                const Ctl c{&a, (int)(tile_base + row), NP, S::KD};
-                const int sel = s_sel[row];
-                const float hf = s_hf[row];
-                if (hf != 0.f) {
-                    // every load first, then the combination
-                    y = ld4(c.vec(sel & 1) + kg);
-                    float4 kv[6];
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) {
-                        const int slot = q == 0 ? ((sel & 2) ? 6 : 0) : q;
-                        kv[q] = (q < s && cA(cf, s, q) != 0.f) ? ld4(c.vec(kVK0 + slot) + kg)
-                                                               : make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) {
-                        const float w = q < s ? hf * cA(cf, s, q) : 0.f;
-                        y.x = fmaf(w, kv[q].x, y.x);
-                        y.y = fmaf(w, kv[q].y, y.y);
-                        y.z = fmaf(w, kv[q].z, y.z);
-                        y.w = fmaf(w, kv[q].w, y.w);
-                    }
-                    if (s == 6) st4(c.vec(1 - (sel & 1)) + kg, y);  // the candidate ynew
-                }
-            }
-            uint2 t[kSplits];
-            split4(y, t);
-            const int off = row * 128 + ((chunk ^ (row & 7)) << 4) + half8 * 2;
-#pragma unroll
-            for (int q = 0; q < kSplits; ++q) *reinterpret_cast<uint2 *>(ytile + q * kYTile + off) = t[q];
+        switch (rhs ? 0 : s) {
+        case 0: produce_rows<NP, 0>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
+        case 1: produce_rows<NP, 1>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
+        case 2: produce_rows<NP, 2>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
+        case 3: produce_rows<NP, 3>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
+        case 4: produce_rows<NP, 4>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
+        case 5: produce_rows<NP, 5>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
+        default: produce_rows<NP, 6>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
         }
         tc::fence_proxy_async_smem();
         tc::mbar_arrive(&p.y_full[ys]);
@@ -330,7 +345,6 @@ using cf32 = cpx<float>;
 template <int NP>
 struct ColCtl {
     static constexpr int R = NP / 32;
-    static constexpr int KD = 2 * NP;
     const DenseArgs &a;
     const KernelArgs &k;
     Group<32> g;
