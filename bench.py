@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-paper", action="store_true",
+                    help="skip the paper's own examples (Sec. 4.1 unitary, Sec. 4.2 trilinear OPA)")
     ap.add_argument("--no-dense", action="store_true",
                     help="skip the dense tensor-core measurement (N = 256, 20,000 trajectories)")
     ap.add_argument("--no-proposal", action="store_true",
@@ -438,6 +440,9 @@ def main():
     if not args.no_ising:
         line["ising_batch"] = ising_batch(Q, torch, stream, world, rank, dist)
         line["gpu_launches"] += line["ising_batch"].pop("launches")
+    if not args.no_paper:
+        line["paper_workloads"] = paper_workloads(Q, torch, stream, world, rank, dist)
+        line["gpu_launches"] += line["paper_workloads"].pop("launches")
     if not args.no_dense:
         line["dense_tensor_core"] = dense_tensor_core(Q, torch, stream, world, rank, dist, pk)
         line["gpu_launches"] += line["dense_tensor_core"].pop("launches")
@@ -495,6 +500,60 @@ def ising_batch(Q, torch, stream, world, rank, dist):
                         "one CUDA-graph launch", "precision": "df64",
             "value": world * sum(counts) / (float(t.item()) / 1e3), "unit": UNIT, "ms_per_step": float(t.item()),
             "observable_error": err, "layouts": [list(x) for x in layouts], "launches": 2 * 5 * 5}
+
+
+def paper_workloads(Q, torch, stream, world, rank, dist):
+    """The paper's own timed examples, as the paper states them: Sec. 4.1 (H =
+    (2 pi/10) sigma_x, C = 0.05 sigma_x, observable sigma_z, psi0 = |0>, t in [0, 10],
+    1,000 trajectories) and Sec. 4.2 (trilinear optical parametric amplifier, 8 x 8
+    x 8 modes = N 512, three damping channels, coherent pump alpha = sqrt 3, three
+    photon-number observables, t in [0, 4], 10,000 trajectories).  Double-float and
+    complex128, each timed end to end through the public API (create with the host
+    problem, run, expect) and as kernel time; the paper's CPU times are context
+    only (another machine, tolerance 1e-7, a Fortran ZVODE solver)."""
+    from paper_1810_03047_gb300 import shards
+    from paper_1810_03047_gb300 import systems as S
+    sid = int(stream.cuda_stream)
+    out = {}
+    launches = 0
+    for name, prob, n, ctx_note in [
+            ("unitary_sec4_1", S.paper_unitary(), 1000,
+             "paper: QTM 2-3 s for 1,000 trajectories on 8 MPI processes (mostly start-up); QuTiP ~0.9 s on "
+             "1 core; Intel i7 4.0 GHz, tolerance 1e-7"),
+            ("trilinear_sec4_2", S.paper_trilinear(), 10000,
+             "paper: timings shown only as a figure (QTM on 32 MPI workers, QuTiP on 4 cores, "
+             "QuantumOptics.jl on 1 core)")]:
+        first, count = shards.shard(world * n, world, rank)
+        res = {}
+        for pname, prec in (("df64", Q.QTM_PREC_DF64), ("c128", Q.QTM_PREC_C128)):
+            ctx = Q.qtm_create(prob, stream=sid, precision=prec)
+            Q.qtm_run_range(ctx, first, count, prob.seed)  # warm-up
+            Q.qtm_expect(ctx)
+            Q.qtm_destroy(ctx)
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx = Q.qtm_create(prob, stream=sid, precision=prec)
+            Q.qtm_run_range(ctx, first, count, prob.seed)
+            mean, _ = Q.qtm_expect(ctx)
+            wall = time.perf_counter() - t0
+            st = Q.qtm_stats(ctx)
+            Q.qtm_destroy(ctx)
+            t = torch.tensor([wall], dtype=torch.float64, device="cuda")
+            if world > 1:
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            res[pname] = {"e2e_s": float(t.item()), "kernel_ms": st["kernel_ms"],
+                          "value": world * count / float(t.item()), "mean": mean}
+            launches += 2 * 5
+        out[name] = {"ntraj": world * count, "unit": UNIT,
+                     "df64": {k: v for k, v in res["df64"].items() if k != "mean"},
+                     "c128": {k: v for k, v in res["c128"].items() if k != "mean"},
+                     "observable_error_df64_vs_c128": float(np.abs(res["df64"]["mean"] - res["c128"]["mean"]).max()),
+                     "steps_per_trajectory": (st["accepted"] + st["rejected"]) / count,
+                     "jumps_per_trajectory": st["jumps"] / count, "context": ctx_note}
+    out["launches"] = launches
+    return out
 
 
 def dense_tensor_core(Q, torch, stream, world, rank, dist, pk, ntraj=20000, sample=2000):

@@ -51,7 +51,8 @@ class OrcProblem(ct.Structure):
     _fields_ = [("dim", ct.c_int32), ("H", OrcOp), ("n_c", ct.c_int32), ("C", ct.POINTER(OrcOp)),
                 ("n_obs", ct.c_int32), ("A", ct.POINTER(OrcOp)), ("psi0", ct.POINTER(ct.c_double)),
                 ("n_t", ct.c_int32), ("t", ct.POINTER(ct.c_double)), ("rtol", ct.c_double),
-                ("atol", ct.c_double), ("max_steps", ct.c_int64)]
+                ("atol", ct.c_double), ("max_steps", ct.c_int64), ("n_drive", ct.c_int32),
+                ("drive", ct.POINTER(OrcOp)), ("drive_coef", ct.POINTER(ct.c_double))]
 
 
 class OrcResult(ct.Structure):
@@ -125,6 +126,15 @@ class _Marshalled:
         self.p.rtol = float(prob.rtol)
         self.p.atol = float(prob.atol)
         self.p.max_steps = int(getattr(prob, "max_steps", 1_000_000))
+        drive = list(getattr(prob, "drive", []) or [])
+        ops_d = [self._op(d[0]) for d in drive]
+        self.darr = (OrcOp * max(1, len(ops_d)))(*ops_d)
+        coef = np.ascontiguousarray(np.array([[float(a), float(w), float(ph)] for _, a, w, ph in drive]
+                                             or [[0.0, 0.0, 0.0]], dtype=np.float64))
+        self.keep.append(coef)
+        self.p.n_drive = len(ops_d)
+        self.p.drive = ct.cast(self.darr, ct.POINTER(OrcOp))
+        self.p.drive_coef = _dptr(coef)
         self.n_t = len(t)
         self.n_obs = len(ops_a)
 

@@ -29,7 +29,11 @@
  *   - the observables Re<psi|A|psi>/<psi|psi> at the output times and their
  *     average over trajectories (Sec. 3, averaging of trajectories);
  *   - a companion Lindblad master-equation integrator (Sec. 2.2, Eq. for
- *     rho-dot) used to check the ensemble statistics on small systems.
+ *     rho-dot) used to check the ensemble statistics on small systems;
+ *   - optionally a time-dependent Hamiltonian H(t) = H + sum_k f_k(t) H_k with
+ *     f_k(t) = a_k cos(omega_k t + phi_k) (Sec. 3: mpi_main takes an extra
+ *     function for a time-dependent Hamiltonian, and the right-hand side sees the
+ *     current time); every right-hand-side evaluation uses the time of its stage.
  *
  * Readings of the paper taken here (the paper is silent or ambiguous on them):
  *   - step (C) draws a fresh uniform c_k for the channel instead of re-using r;
@@ -76,6 +80,9 @@ typedef struct {
     const double *t;         /* n_t, strictly increasing */
     double rtol, atol;
     int64_t max_steps;       /* attempted steps per trajectory */
+    int32_t n_drive;         /* time-dependent terms (0: H is constant) */
+    const orc_op *drive;     /* n_drive Hermitian H_k */
+    const double *drive_coef;/* 3 * n_drive: a_k, omega_k, phi_k of f_k(t) = a_k cos(omega_k t + phi_k) */
 } orc_problem;
 
 typedef struct {
@@ -319,13 +326,14 @@ static void dp_dense_weights(double th, double w[7])
     w[6] = th2 * (th - 1.0) + q * 10.0 * (7414447.0 - 829305.0 * th) / 29380423.0;
 }
 
-typedef void (*rhs_fn)(void *ctx, const cplx *y, cplx *dy);
+typedef void (*rhs_fn)(void *ctx, double t, const cplx *y, cplx *dy);
 
-/* One attempted step of size h from y with K[0] = f(y) already known.
- * Fills K[1..6] (K[6] = f(ynew)), ynew, and returns the scaled RMS error norm
+/* One attempted step of size h from (t, y) with K[0] = f(t, y) already known.
+ * Fills K[1..6] (K[s] = f(t + c_s h, y_s), K[6] = f(t + h, ynew)), ynew, and
+ * returns the scaled RMS error norm
  *   sqrt( (1/n) sum_i |e_i|^2 / sc_i^2 ),  e = h sum_j (b_j - bhat_j) k_j,
  *   sc_i = atol + rtol max(|y_i|, |ynew_i|)   (HNW Sec. II.4, Eq. (4.10)-(4.11)). */
-static double dp_step(int n, rhs_fn f, void *ctx, const cplx *y, cplx *K[7], double h,
+static double dp_step(int n, rhs_fn f, void *ctx, double t, const cplx *y, cplx *K[7], double h,
                       cplx *ynew, cplx *ytmp, double rtol, double atol)
 {
     for (int s = 1; s < 7; s++) {
@@ -335,7 +343,7 @@ static double dp_step(int n, rhs_fn f, void *ctx, const cplx *y, cplx *K[7], dou
             for (int j = 0; j < s; j++) acc += DP_A[s][j] * K[j][i];
             ys[i] = y[i] + h * acc;
         }
-        f(ctx, ys, K[s]);
+        f(ctx, t + DP_C[s] * h, ys, K[s]);
     }
     double sum = 0.0;
     for (int i = 0; i < n; i++) {
@@ -365,7 +373,7 @@ static void dp_dense(int n, const cplx *y, cplx *K[7], double h, double theta, c
 /* Starting step size (HNW Sec. II.4, "Starting step size", with p = 4):
  * h0 from ||y0|| / ||f0||, one explicit Euler step to estimate the second
  * derivative, h1 = (0.01 / max(d1, d2))^(1/5), h = min(100 h0, h1). */
-static double dp_initial_step(int n, rhs_fn f, void *ctx, const cplx *y0, const cplx *f0,
+static double dp_initial_step(int n, rhs_fn f, void *ctx, double t0, const cplx *y0, const cplx *f0,
                               double span, double rtol, double atol, cplx *y1, cplx *f1,
                               int64_t *rhs_count)
 {
@@ -381,7 +389,7 @@ static double dp_initial_step(int n, rhs_fn f, void *ctx, const cplx *y0, const 
     double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
     if (h0 > span) h0 = span;
     for (int i = 0; i < n; i++) y1[i] = y0[i] + h0 * f0[i];
-    f(ctx, y1, f1);
+    f(ctx, t0 + h0, y1, f1);
     (*rhs_count)++;
     double d2 = 0.0;
     for (int i = 0; i < n; i++) {
@@ -413,7 +421,7 @@ typedef struct {
     const cplx *M;
 } dense_ctx;
 
-static void dense_rhs(void *vctx, const cplx *y, cplx *dy)
+static void dense_rhs(void *vctx, double t, const cplx *y, cplx *dy)
 {
     const dense_ctx *c = vctx;
     for (int i = 0; i < c->n; i++) {
@@ -437,8 +445,8 @@ int orc_dopri5_fixed(int n, const double *M, const double *y0, double h, int nst
     for (int j = 0; j < 7; j++) K[j] = buf + (size_t)(3 + j) * n;
     memcpy(y, y0, sizeof(cplx) * n);
     for (int s = 0; s < nsteps; s++) {
-        dense_rhs(&ctx, y, K[0]);
-        dp_step(n, dense_rhs, &ctx, y, K, h, ynew, ytmp, 1.0, 1.0);
+        dense_rhs(&ctx, 0.0, y, K[0]);
+        dp_step(n, dense_rhs, &ctx, 0.0, y, K, h, ynew, ytmp, 1.0, 1.0);
         if (s == nsteps - 1) {
             if (err_out) {
                 cplx *e = (cplx *)err_out;
@@ -471,17 +479,40 @@ typedef struct {
     int n_obs;
     csr *A;
     cplx *psi0;  /* normalised */
+    int n_drive;
+    csr *D;      /* -i H_k of the time-dependent terms */
     const orc_problem *p;
 } model;
 
-static void model_rhs(void *vctx, const cplx *y, cplx *dy)
+/* The right-hand side's context: the shared, read-only model and this
+ * thread's scratch vector for the time-dependent terms. */
+typedef struct {
+    const model *m;
+    cplx *dtmp;
+} rhs_ctx;
+
+/* f_k(t) = a_k cos(omega_k t + phi_k) */
+static double drive_coef(const orc_problem *p, int k, double t)
 {
-    const model *m = vctx;
+    const double *c = p->drive_coef + 3 * k;
+    return c[0] * cos(c[1] * t + c[2]);
+}
+
+/* dpsi/dt = M psi + sum_k f_k(t) (-i H_k) psi */
+static void model_rhs(void *vctx, double t, const cplx *y, cplx *dy)
+{
+    const rhs_ctx *c = vctx;
+    const model *m = c->m;
     csr_mv(&m->M, y, dy);
+    for (int k = 0; k < m->n_drive; k++) {
+        double f = drive_coef(m->p, k, t);
+        csr_mv(&m->D[k], y, c->dtmp);
+        for (int i = 0; i < m->n; i++) dy[i] += f * c->dtmp[i];
+    }
 }
 
 typedef struct {
-    cplx *psi, *ynew, *ytmp, *K[7], *yd, *cy, *ay;
+    cplx *psi, *ynew, *ytmp, *K[7], *yd, *cy, *ay, *dtmp;
 } workspace;
 
 /* Re and Im of <y|A_k|y>/<y|y> at output time index j */
@@ -560,9 +591,10 @@ static int run_trajectory(const model *m, uint64_t seed, int64_t traj, workspace
     record_outputs(m, w->psi, w->ay, 0, o->obs_re, o->obs_im);
     int j = 1; /* next output index */
 
-    model_rhs((void *)m, w->psi, w->K[0]);
+    rhs_ctx rc = {m, w->dtmp};
+    model_rhs(&rc, t, w->psi, w->K[0]);
     rhs++;
-    double h = dp_initial_step(n, model_rhs, (void *)m, w->psi, w->K[0], t_end - t, rtol, atol,
+    double h = dp_initial_step(n, model_rhs, &rc, t, w->psi, w->K[0], t_end - t, rtol, atol,
                                w->ytmp, w->ynew, &rhs);
     int rejected_before = 0;
 
@@ -581,7 +613,7 @@ static int run_trajectory(const model *m, uint64_t seed, int64_t traj, workspace
         if (h < 1e-14 * fmax(1.0, fabs(t))) { status = ORC_ERR_STEPSIZE; break; }
 
         /* (B): integrate dpsi/dt = -i H_eff psi over [t, t + h] */
-        double err = dp_step(n, model_rhs, (void *)m, w->psi, w->K, h, w->ynew, w->ytmp, rtol, atol);
+        double err = dp_step(n, model_rhs, &rc, t, w->psi, w->K, h, w->ynew, w->ytmp, rtol, atol);
         rhs += 6;
         attempts++;
         if (!(err <= 1.0)) {
@@ -646,7 +678,7 @@ static int run_trajectory(const model *m, uint64_t seed, int64_t traj, workspace
             k++;
             orc_uniforms(seed, traj, k, &r, &c);
             t = tau;
-            model_rhs((void *)m, w->psi, w->K[0]);
+            model_rhs(&rc, t, w->psi, w->K[0]);
             rhs++;
             rejected_before = 0;
             continue;
@@ -693,9 +725,31 @@ static void model_free(model *m)
     csr_free(&m->M);
     for (int i = 0; i < m->n_c; i++) csr_free(&m->C[i]);
     for (int i = 0; i < m->n_obs; i++) csr_free(&m->A[i]);
+    for (int i = 0; i < m->n_drive; i++) csr_free(&m->D[i]);
     free(m->C);
     free(m->A);
+    free(m->D);
     free(m->psi0);
+}
+
+/* D = -i H_k of each time-dependent term */
+static int drive_init(const orc_problem *p, int n, int *n_drive, csr **D)
+{
+    *n_drive = 0;
+    *D = NULL;
+    if (p->n_drive <= 0) return ORC_OK;
+    if (!p->drive || !p->drive_coef) return ORC_ERR_ARG;
+    *D = calloc((size_t)p->n_drive, sizeof(csr));
+    if (!*D) return ORC_ERR_NOMEM;
+    for (int k = 0; k < p->n_drive; k++) {
+        if (p->drive[k].n != n) return ORC_ERR_ARG;
+        int st = csr_from_op(&p->drive[k], &(*D)[k]);
+        if (st) return st;
+        ++*n_drive;
+        csr *d = &(*D)[k];
+        for (int e = 0; e < d->row_ptr[d->n]; e++) d->val[e] *= -I;
+    }
+    return ORC_OK;
 }
 
 static int model_init(const orc_problem *p, model *m)
@@ -722,6 +776,7 @@ static int model_init(const orc_problem *p, model *m)
         if ((st = csr_from_op(&p->C[i], &m->C[i]))) return st;
     for (int i = 0; i < p->n_obs; i++)
         if ((st = csr_from_op(&p->A[i], &m->A[i]))) return st;
+    if ((st = drive_init(p, n, &m->n_drive, &m->D))) return st;
     double nn = 0.0;
     for (int i = 0; i < n; i++) {
         m->psi0[i] = p->psi0[2 * i] + I * p->psi0[2 * i + 1];
@@ -748,11 +803,11 @@ static void *worker(void *varg)
     const model *m = a->m;
     int n = m->n;
     const orc_problem *p = m->p;
-    cplx *buf = calloc((size_t)n * 15, sizeof(cplx));
+    cplx *buf = calloc((size_t)n * 16, sizeof(cplx));
     if (!buf) { a->status = ORC_ERR_NOMEM; return NULL; }
     workspace w;
     w.psi = buf; w.ynew = buf + n; w.ytmp = buf + 2 * n; w.yd = buf + 3 * n;
-    w.cy = buf + 4 * n; w.ay = buf + 5 * n;
+    w.cy = buf + 4 * n; w.ay = buf + 5 * n; w.dtmp = buf + 15 * n;
     for (int j = 0; j < 7; j++) w.K[j] = buf + (size_t)(6 + j) * n;
     orc_result *res = a->res;
     size_t per = (size_t)p->n_t * p->n_obs;
@@ -820,6 +875,9 @@ typedef struct {
     csr *C;
     csr *CdC;   /* C_n^dag C_n */
     cplx *tmp, *tmp2;
+    int n_drive;
+    csr *Hd;    /* the time-dependent terms' H_k */
+    const orc_problem *p;
 } lind_model;
 
 /* Y = A X for CSR A and dense row-major X */
@@ -848,7 +906,7 @@ static void mm_csr_dag(const cplx *X, const csr *a, cplx *Y, int n)
         }
 }
 
-static void lindblad_rhs(void *vctx, const cplx *rho, cplx *drho)
+static void lindblad_rhs(void *vctx, double t, const cplx *rho, cplx *drho)
 {
     lind_model *L = vctx;
     int n = L->n;
@@ -857,6 +915,13 @@ static void lindblad_rhs(void *vctx, const cplx *rho, cplx *drho)
     csr_mm(&L->H, rho, L->tmp, n);
     mm_csr_dag(rho, &L->H, L->tmp2, n);
     for (size_t i = 0; i < nn; i++) drho[i] = -I * (L->tmp[i] - L->tmp2[i]);
+    /* -i f_k(t) [H_k, rho] */
+    for (int k = 0; k < L->n_drive; k++) {
+        double f = drive_coef(L->p, k, t);
+        csr_mm(&L->Hd[k], rho, L->tmp, n);
+        mm_csr_dag(rho, &L->Hd[k], L->tmp2, n);
+        for (size_t i = 0; i < nn; i++) drho[i] += -I * f * (L->tmp[i] - L->tmp2[i]);
+    }
     for (int c = 0; c < L->n_c; c++) {
         csr_mm(&L->C[c], rho, L->tmp, n);          /* C rho */
         mm_csr_dag(L->tmp, &L->C[c], L->tmp2, n);  /* C rho C^dag */
@@ -907,6 +972,17 @@ int orc_lindblad(const orc_problem *p, double rtol, double atol, double *out, do
         csr_from_dense(n, dense, &L.CdC[c]);
     }
     for (int k = 0; k < p->n_obs; k++) csr_from_op(&p->A[k], &A[k]);
+    L.p = p;
+    if (p->n_drive > 0) {
+        if (!p->drive || !p->drive_coef) return ORC_ERR_ARG;
+        L.Hd = calloc((size_t)p->n_drive, sizeof(csr));
+        if (!L.Hd) return ORC_ERR_NOMEM;
+        for (int k = 0; k < p->n_drive; k++) {
+            if (p->drive[k].n != n) return ORC_ERR_ARG;
+            if ((st = csr_from_op(&p->drive[k], &L.Hd[k]))) return st;
+            L.n_drive++;
+        }
+    }
     L.tmp = buf;
     L.tmp2 = buf + nn;
     cplx *rho = buf + 2 * nn, *rnew = buf + 3 * nn, *rtmp = buf + 4 * nn, *rd = buf + 5 * nn;
@@ -931,8 +1007,8 @@ int orc_lindblad(const orc_problem *p, double rtol, double atol, double *out, do
     double t = p->t[0], t_end = p->t[p->n_t - 1];
     int j = 1;
     int64_t rhs = 0;
-    lindblad_rhs(&L, rho, K[0]);
-    double h = dp_initial_step((int)nn, lindblad_rhs, &L, rho, K[0], t_end - t, rtol, atol, rtmp,
+    lindblad_rhs(&L, t, rho, K[0]);
+    double h = dp_initial_step((int)nn, lindblad_rhs, &L, t, rho, K[0], t_end - t, rtol, atol, rtmp,
                                rnew, &rhs);
     int rejected_before = 0;
     int status = ORC_OK;
@@ -944,7 +1020,7 @@ int orc_lindblad(const orc_problem *p, double rtol, double atol, double *out, do
             h = t_end - t;
             last = 1;
         }
-        double err = dp_step((int)nn, lindblad_rhs, &L, rho, K, h, rnew, rtmp, rtol, atol);
+        double err = dp_step((int)nn, lindblad_rhs, &L, t, rho, K, h, rnew, rtmp, rtol, atol);
         if (!(err <= 1.0)) {
             if (!isfinite(err)) { status = ORC_ERR_NONFINITE; break; }
             double fac = DP_SAFETY * pow(err, -0.2);
@@ -979,6 +1055,8 @@ int orc_lindblad(const orc_problem *p, double rtol, double atol, double *out, do
         csr_free(&L.CdC[c]);
     }
     for (int k = 0; k < p->n_obs; k++) csr_free(&A[k]);
+    for (int k = 0; k < L.n_drive; k++) csr_free(&L.Hd[k]);
+    free(L.Hd);
     free(L.C);
     free(L.CdC);
     free(A);

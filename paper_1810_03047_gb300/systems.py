@@ -24,7 +24,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import List, Optional
+from typing import List, Optional, Tuple
 
 import numpy as np
 import scipy.linalg
@@ -47,6 +47,8 @@ class Problem:
     output times (``t[0]`` is the start time), ``rtol``/``atol``: integrator
     tolerances, ``ntraj``/``seed``: ensemble size and random-stream key.
     ``dense``: the operators are dense matrices (pass them in dense format).
+    ``drive``: time-dependent terms (H_k, a_k, omega_k, phi_k) adding
+    a_k cos(omega_k t + phi_k) H_k to H (each H_k Hermitian).
     """
 
     name: str
@@ -62,6 +64,7 @@ class Problem:
     dense: bool = False
     max_steps: int = 1_000_000
     obs_names: Optional[List[str]] = None
+    drive: List[Tuple[sp.csr_matrix, float, float, float]] = dataclasses.field(default_factory=list)
 
     @property
     def dim(self) -> int:
@@ -243,6 +246,35 @@ def ising_batch(Ls=(6, 7, 8, 9, 10)) -> List[Problem]:
     return [ising_chain(L) for L in Ls]
 
 
+def driven_dephasing_qubit(ntraj: int = 500, seed: int = 1, a: float = 1.3, omega: float = 2.0,
+                           phi: float = 0.4, gamma: float = 0.1, n_t: int = 101,
+                           t_end: float = 10.0) -> Problem:
+    """Time-dependent Hamiltonian with a closed form: H(t) = a cos(omega t + phi) sigma_z
+    (the constant part of H is zero), dephasing C = sqrt(gamma) sigma_z, psi0 =
+    |+> = (|0> + |1>)/sqrt 2, observables sigma_x and sigma_y.  With F(t) = the
+    integral of the coefficient, a trajectory with N(t) jumps by time t has
+    <sigma_x> = (-1)^N cos 2F and <sigma_y> = (-1)^N sin 2F; the ensemble mean of
+    <sigma_x> is exp(-2 gamma t) cos 2F."""
+    H0 = sp.csr_matrix((2, 2), dtype=np.complex128)
+    psi0 = np.array([1.0, 1.0], dtype=np.complex128) / math.sqrt(2.0)
+    return Problem("driven_dephasing_qubit", H0, [_csr(math.sqrt(gamma) * sigma_z())],
+                   [sigma_x(), sigma_y()], psi0, np.linspace(0.0, t_end, n_t), 1e-8, 1e-10, ntraj, seed,
+                   obs_names=["sigma_x", "sigma_y"], drive=[(sigma_z(), a, omega, phi)])
+
+
+def jaynes_cummings_pulsed(ntraj: int = 2000, seed: int = 1, n_fock: int = 30, n_t: int = 201,
+                           t_end: float = 20.0, g: float = 1.0, E: float = 0.8, omega: float = 0.7,
+                           kappa: float = 0.2, gamma: float = 0.05) -> Problem:
+    """The damped Jaynes-Cummings system with a modulated cavity drive instead of a
+    constant one: H(t) = g (a^dag sigma_- + a sigma_+) + E cos(omega t) (a + a^dag),
+    C = {sqrt(kappa) a, sqrt(gamma) sigma_-}, psi0 = |0> (x) |e>, observables
+    a^dag a and sigma_+ sigma_-."""
+    base = jaynes_cummings_driven(ntraj=ntraj, seed=seed, n_fock=n_fock, n_t=n_t, t_end=t_end, g=g, E=0.0,
+                                  kappa=kappa, gamma=gamma)
+    a = kron(destroy(n_fock), eye(2))
+    return base.with_(name="jaynes_cummings_pulsed", drive=[(_csr(a + dag(a)), E, omega, 0.0)])
+
+
 def learned_proposal_system(ntraj: int = 200000, seed: int = 1) -> Problem:
     """The Jaynes-Cummings system above at the ensemble size of the learned-proposal study."""
     return jaynes_cummings_driven(ntraj=ntraj, seed=seed).with_(name="learned_proposal_jc")
@@ -325,6 +357,8 @@ def by_name(name: str, **kw) -> Problem:
         "paper_jaynes_cummings": paper_jaynes_cummings,
         "paper_photon_birth_death": paper_photon_birth_death,
         "fock_decay": fock_decay,
+        "driven_dephasing_qubit": driven_dephasing_qubit,
+        "jaynes_cummings_pulsed": jaynes_cummings_pulsed,
     }
     if name.startswith("ising_L"):
         return ising_chain(int(name[len("ising_L"):]), **kw)

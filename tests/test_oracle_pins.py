@@ -396,3 +396,62 @@ def test_argument_errors_and_limits(orc):
     res = orc.mcwf(one, ntraj=3)
     assert res["rc"] == 0 and res["obs"].shape == (3, 1, 2)
     assert np.all(res["obs"][:, 0, 0] == 0.0)  # |g> has no excitation
+
+
+# ---------------------------------------------------------------------------
+# time-dependent Hamiltonian H(t) = H + sum_k a_k cos(omega_k t + phi_k) H_k
+# (Sec. 3: mpi_main accepts a function for a time-dependent Hamiltonian)
+# ---------------------------------------------------------------------------
+
+def _phase(prob):
+    (_, a, w, ph), = prob.drive
+    return (a / w) * (np.sin(w * prob.t + ph) - np.sin(ph))
+
+
+def test_drive_dephasing_closed_form_per_trajectory(orc):
+    """H(t) = a cos(wt + phi) sigma_z with sigma_z dephasing: between jumps psi0 = |+>
+    only picks up the relative phase 2F(t), F = (a/w)(sin(wt+phi) - sin phi), and each
+    jump flips its sign, so <sigma_x> = (-1)^N cos 2F, <sigma_y> = (-1)^N sin 2F with
+    N the jumps up to t.  Checks that the stage times reach the coefficient (a drive
+    evaluated at the step start would miss F by O(h))."""
+    prob = S.driven_dephasing_qubit(ntraj=300).with_(rtol=1e-10, atol=1e-12)
+    res = orc.mcwf(prob, ntraj=300, max_jumps=64)
+    assert res["rc"] == 0 and res["n_jumps"].sum() > 150
+    F = _phase(prob)
+    for i in range(300):
+        jt = res["jump_t"][i, :res["n_jumps"][i]]
+        N = (jt[None, :] <= prob.t[:, None]).sum(axis=1)
+        np.testing.assert_allclose(res["obs"][i, :, 0], (-1.0) ** N * np.cos(2 * F), atol=1e-8)
+        np.testing.assert_allclose(res["obs"][i, :, 1], (-1.0) ** N * np.sin(2 * F), atol=1e-8)
+
+
+def test_drive_lindblad_closed_form(orc):
+    """The master equation with the same drive: <sigma_x> = exp(-2 gamma t) cos 2F."""
+    prob = S.driven_dephasing_qubit()
+    L, _ = orc.lindblad(prob, 1e-11, 1e-13)
+    F = _phase(prob)
+    decay = np.exp(-2 * 0.1 * prob.t)
+    np.testing.assert_allclose(L[:, 0], decay * np.cos(2 * F), atol=1e-9)
+    np.testing.assert_allclose(L[:, 1], decay * np.sin(2 * F), atol=1e-9)
+
+
+def test_constant_drive_equals_static_term(orc):
+    """A term with omega = phi = 0 is the constant a H_k: the same trajectories as
+    with a H_k folded into H (the same jumps; rounding-level differences only)."""
+    stat = S.jaynes_cummings_driven(n_fock=8, n_t=41, t_end=8.0, E=0.5)
+    base = S.jaynes_cummings_driven(n_fock=8, n_t=41, t_end=8.0, E=0.0)
+    a = S.kron(S.destroy(8), S.eye(2))
+    drv = base.with_(drive=[(a + S.dag(a), 0.5, 0.0, 0.0)])
+    r1 = orc.mcwf(stat, ntraj=60)
+    r2 = orc.mcwf(drv, ntraj=60)
+    np.testing.assert_array_equal(r1["n_jumps"], r2["n_jumps"])
+    np.testing.assert_allclose(r1["obs"], r2["obs"], atol=1e-7)
+
+
+def test_drive_ensemble_matches_lindblad(orc):
+    """Algorithm 1 with a modulated cavity drive against the driven master equation."""
+    prob = S.jaynes_cummings_pulsed(n_fock=8, n_t=81, t_end=8.0)
+    res = orc.mcwf(prob, ntraj=1500)
+    assert res["rc"] == 0
+    L, _ = orc.lindblad(prob, 1e-10, 1e-12)
+    _check_against_lindblad(res["obs"], L)
