@@ -336,6 +336,18 @@ const char *qtm_last_error(const qtm_ctx *ctx);
 /* Name of a status code, e.g. "QTM_ERR_ARG". */
 const char *qtm_status_string(qtm_status status);
 
+/* Time-dependent Hamiltonian (Sec. 3: mpi_main accepts an extra function for a
+ * time-dependent H, and the right-hand side sees the current time):
+ *   H(t) = H + sum_k a_k cos(omega_k t + phi_k) H_k,   k < n_terms <= 8.
+ * H: n_terms Hermitian operators of the context's dimension (HOST, copied);
+ * coef: HOST, [n_terms][3] = a_k, omega_k, phi_k (finite).  Every right-hand-side
+ * evaluation of a trajectory uses the time of its Dormand-Prince stage (and
+ * t0 + h0 in the starting-step estimate); the collapse operators, observables and
+ * the jump rule are unchanged.  n_terms = 0 removes the terms.  Applies to later
+ * runs; QTM_ERR_UNSUPPORTED for QTM_PREC_BF16X6 (its operator is constant) or
+ * when the operators no longer fit a kernel (reported by qtm_run). */
+qtm_status qtm_set_drive(qtm_ctx *ctx, int32_t n_terms, const qtm_op *H, const double *coef);
+
 /* Batched right-hand side: my[v] = M y[v] with M = -i H_eff, for n_vec vectors
  * y (HOST, [n_vec][dim] complex, interleaved (re, im) doubles; rounded to FP32)
  * through the tensor-core engine's product (QTM_PREC_BF16X6 contexts only;

@@ -8,7 +8,7 @@ namespace qtm {
 
 cudaError_t launch_mcwf_c128_prop(const KernelArgs &a, cudaStream_t stream, LaunchInfo *info)
 {
-    return launch_small<ArF64, true>(a, stream, info);
+    return launch_small<ArF64, kFeatProposal>(a, stream, info);
 }
 
 }  // namespace qtm

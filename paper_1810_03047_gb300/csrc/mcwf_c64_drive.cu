@@ -1,0 +1,14 @@
+// mcwf_c64_drive.cu -- complex64 instantiations of the trajectory kernel with the
+// time-dependent terms a_k cos(omega_k t + phi_k) (-i H_k) compiled into every
+// right-hand-side evaluation, for every lane layout.  The plain instantiations
+// carry none of that code.
+#include "mcwf_kernel.cuh"
+
+namespace qtm {
+
+cudaError_t launch_mcwf_c64_drive(const KernelArgs &a, cudaStream_t stream, LaunchInfo *info)
+{
+    return a.G <= 32 ? launch_small<ArF32, kFeatDrive>(a, stream, info) : launch_large<ArF32, kFeatDrive>(a, stream, info);
+}
+
+}  // namespace qtm

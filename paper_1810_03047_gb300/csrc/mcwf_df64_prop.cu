@@ -8,7 +8,7 @@ namespace qtm {
 
 cudaError_t launch_mcwf_df64_prop(const KernelArgs &a, cudaStream_t stream, LaunchInfo *info)
 {
-    return launch_small<ArDF, true>(a, stream, info);
+    return launch_small<ArDF, kFeatProposal>(a, stream, info);
 }
 
 }  // namespace qtm

@@ -144,6 +144,30 @@ __device__ __noinline__ void dense_rows(const Coefs<Ar> &C, const Lanes<Ar, G, R
     }
 }
 
+// The time-dependent part of the right-hand side: out[row] += f_k(time) (-i H_k x)[row]
+// on the lane's rows, f_k = a_k cos(omega_k time + phi_k) in FP64 (x is the
+// synchronised exchange vector the product M x was taken of).
+template <class Ar, int G, int R>
+__device__ __noinline__ void drive_rows(const KernelArgs &a, const int *si, const typename Ar::real *sv,
+                                        const typename Ar::cplx *x, typename Ar::cplx *out, int gl,
+                                        double time)
+{
+    for (int k = 0; k < a.n_drive; ++k) {
+        const typename Ar::coef f = Ar::coef_of(a.drive[k][0] * cos(a.drive[k][1] * time + a.drive[k][2]));
+        const CsrView<Ar> D = csr_view<Ar>(a.op[a.drive_op0 + k], si, sv);
+#pragma unroll 1
+        for (int r = 0; r < R; ++r) {
+            const typename Ar::cplx v = spmv_row<Ar, G>(D, x, gl, r);
+            const int row = gl + G * r;
+            if (row < a.n) {
+                typename Ar::acc acc = Ar::zero();
+                Ar::axpy(acc, f, v);
+                out[row] = Ar::add_scaled(out[row], Ar::coef_of(1.0), acc);
+            }
+        }
+    }
+}
+
 // Output j: Re<y|A_k|y>/<y|y> for every observable, written by lane 0.  y is in
 // the exchange half `y` and the group has synchronised after writing it.
 // When obs is not NULL, lane 0 also stores the first two values there as floats.
@@ -422,11 +446,16 @@ __device__ __noinline__ int apply_jump(const KernelArgs &a, Group<G> g, const in
     return ch;
 }
 
-template <class Ar, int G, int R, bool PROP>
+// Compile-time features of an instantiation: the plain kernels carry neither.
+enum Feature { kFeatProposal = 1, kFeatDrive = 2 };
+
+template <class Ar, int G, int R, int FEAT>
 __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int *si,
                                const typename Ar::real *sv, const Coefs<Ar> &C, Lanes<Ar, G, R> &L,
                                float *hscratch, PropState *P, long long il)
 {
+    constexpr bool PROP = (FEAT & kFeatProposal) != 0;
+    constexpr bool DRIVE = (FEAT & kFeatDrive) != 0;
     using cplx = typename Ar::cplx;
     const int n = a.n;
     const int gl = g.gl;
@@ -469,6 +498,7 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
     int j = 1;
     bool proposed = false;
     spmv_rows<Ar, G, R>(M, b, L.kq(0), gl, n);
+    if constexpr (DRIVE) drive_rows<Ar, G, R>(a, si, sv, b, L.kq(0), gl, t);
     ++n_rhs;
 
     // starting step (Hairer, Norsett & Wanner, Sec. II.4), in FP64 scalars
@@ -505,6 +535,7 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
         g.sync();
         cplx *f1 = L.kq(1);  // scratch: K_1 is recomputed by the first step
         spmv_rows<Ar, G, R>(M, b, f1, gl, n);
+        if constexpr (DRIVE) drive_rows<Ar, G, R>(a, si, sv, b, f1, gl, t + h0);
         ++n_rhs;
         double d2 = 0.0;
 #pragma unroll
@@ -581,6 +612,7 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
             }
             g.sync();
             spmv_rows<Ar, G, R>(M, b, L.kq(s), gl, n);
+            if constexpr (DRIVE) drive_rows<Ar, G, R>(a, si, sv, b, L.kq(s), gl, t + DP5::c(s) * h);
         }
         n_rhs += 6;
         ++attempts;
@@ -661,6 +693,7 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
             }
             g.sync();
             spmv_rows<Ar, G, R>(M, b, L.kq(0), gl, n);
+            if constexpr (DRIVE) drive_rows<Ar, G, R>(a, si, sv, b, L.kq(0), gl, t);
             ++n_rhs;
             rejected_before = false;
             continue;
@@ -726,7 +759,7 @@ __host__ __device__ constexpr int block_for_group() { return G <= 32 ? 128 : 256
 template <int G>
 __host__ __device__ constexpr bool ops_in_shared() { return G <= 32; }
 
-template <class Ar, int G, int R, int BLOCK, bool PROP>
+template <class Ar, int G, int R, int BLOCK, int FEAT>
 __global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 1)) mcwf_kernel(const __grid_constant__ KernelArgs a)
 {
     using cplx = typename Ar::cplx;
@@ -761,6 +794,7 @@ __global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 1)) mcwf_kernel(const __
     Lanes<Ar, G, R> L{reinterpret_cast<cplx *>(smem + a.smem_ybuf_offset) + (threadIdx.x / G) * kNumSlots * (G * R),
                       g.gl, a.n, 0};
     unsigned char *pbase = smem + a.smem_mlp_offset + (size_t)(threadIdx.x / G) * kPropStride;
+    constexpr bool PROP = (FEAT & kFeatProposal) != 0;
     float *hscratch = PROP ? reinterpret_cast<float *>(pbase) : nullptr;
     PropState *P = PROP ? reinterpret_cast<PropState *>(pbase + kMlpHidden * sizeof(float)) : nullptr;
     for (;;) {
@@ -768,12 +802,12 @@ __global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 1)) mcwf_kernel(const __
         if (g.gl == 0) i = atomicAdd(a.queue, 1ULL);
         i = g.bcast0(i);
         if ((long long)i >= a.ntraj) break;
-        run_trajectory<Ar, G, R, PROP>(a, g, si, sv, *C, L, hscratch, P, (long long)i);
+        run_trajectory<Ar, G, R, FEAT>(a, g, si, sv, *C, L, hscratch, P, (long long)i);
     }
 }
 
 // Shared-memory layout and occupancy-sized persistent launch of one instantiation.
-template <class Ar, int G, int R, bool PROP = false>
+template <class Ar, int G, int R, int FEAT = 0>
 cudaError_t launch_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInfo *info)
 {
     using cplx = typename Ar::cplx;
@@ -785,7 +819,7 @@ cudaError_t launch_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInf
     const size_t vb = ops_in_shared<G>() ? al16((size_t)a.n_vals * sizeof(typename Ar::real)) : 0;
     const size_t cb = al16(sizeof(Coefs<Ar>));
     const size_t sb = al16((size_t)GROUPS * (Group<G>::kWarps + 1) * 8);
-    const size_t mb = PROP ? (size_t)GROUPS * kPropStride : 0;
+    const size_t mb = (FEAT & kFeatProposal) ? (size_t)GROUPS * kPropStride : 0;
     a.smem_vals_offset = (int)ib;
     a.smem_coef_offset = (int)(ib + vb);
     a.smem_scratch_offset = (int)(ib + vb + cb);
@@ -793,7 +827,7 @@ cudaError_t launch_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInf
     a.smem_ybuf_offset = (int)(ib + vb + cb + sb + mb);
     const size_t smem = ib + vb + cb + sb + mb + (size_t)GROUPS * kNumSlots * G * R * sizeof(cplx);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    auto kern = mcwf_kernel<Ar, G, R, BLOCK, PROP>;
+    auto kern = mcwf_kernel<Ar, G, R, BLOCK, FEAT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     // the trajectory state lives in shared memory: ask for the largest carveout
@@ -821,30 +855,30 @@ cudaError_t launch_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInf
 // The instantiation for the layout the operators were packed with (a.G, a.R):
 // single-warp groups here, multi-warp groups in launch_large.  The layouts are
 // those of layout_candidates.
-template <class Ar, bool PROP = false>
+template <class Ar, int FEAT = 0>
 cudaError_t launch_small(const KernelArgs &a, cudaStream_t stream, LaunchInfo *info)
 {
-    if (a.G == 1 && a.R == 2) return launch_instance<Ar, 1, 2, PROP>(a, stream, info);
-    if (a.G == 4 && a.R == 2) return launch_instance<Ar, 4, 2, PROP>(a, stream, info);
-    if (a.G == 4 && a.R == 4) return launch_instance<Ar, 4, 4, PROP>(a, stream, info);
-    if (a.G == 8 && a.R == 2) return launch_instance<Ar, 8, 2, PROP>(a, stream, info);
-    if (a.G == 8 && a.R == 4) return launch_instance<Ar, 8, 4, PROP>(a, stream, info);
-    if (a.G == 16 && a.R == 2) return launch_instance<Ar, 16, 2, PROP>(a, stream, info);
-    if (a.G == 16 && a.R == 4) return launch_instance<Ar, 16, 4, PROP>(a, stream, info);
-    if (a.G == 32 && a.R == 2) return launch_instance<Ar, 32, 2, PROP>(a, stream, info);
-    if (a.G == 32 && a.R == 4) return launch_instance<Ar, 32, 4, PROP>(a, stream, info);
+    if (a.G == 1 && a.R == 2) return launch_instance<Ar, 1, 2, FEAT>(a, stream, info);
+    if (a.G == 4 && a.R == 2) return launch_instance<Ar, 4, 2, FEAT>(a, stream, info);
+    if (a.G == 4 && a.R == 4) return launch_instance<Ar, 4, 4, FEAT>(a, stream, info);
+    if (a.G == 8 && a.R == 2) return launch_instance<Ar, 8, 2, FEAT>(a, stream, info);
+    if (a.G == 8 && a.R == 4) return launch_instance<Ar, 8, 4, FEAT>(a, stream, info);
+    if (a.G == 16 && a.R == 2) return launch_instance<Ar, 16, 2, FEAT>(a, stream, info);
+    if (a.G == 16 && a.R == 4) return launch_instance<Ar, 16, 4, FEAT>(a, stream, info);
+    if (a.G == 32 && a.R == 2) return launch_instance<Ar, 32, 2, FEAT>(a, stream, info);
+    if (a.G == 32 && a.R == 4) return launch_instance<Ar, 32, 4, FEAT>(a, stream, info);
     return cudaErrorInvalidValue;
 }
 
-template <class Ar>
+template <class Ar, int FEAT = 0>
 cudaError_t launch_large(const KernelArgs &a, cudaStream_t stream, LaunchInfo *info)
 {
-    if (a.G == 64 && a.R == 2) return launch_instance<Ar, 64, 2>(a, stream, info);
-    if (a.G == 64 && a.R == 4) return launch_instance<Ar, 64, 4>(a, stream, info);
-    if (a.G == 128 && a.R == 2) return launch_instance<Ar, 128, 2>(a, stream, info);
-    if (a.G == 128 && a.R == 4) return launch_instance<Ar, 128, 4>(a, stream, info);
-    if (a.G == 256 && a.R == 2) return launch_instance<Ar, 256, 2>(a, stream, info);
-    if (a.G == 256 && a.R == 4) return launch_instance<Ar, 256, 4>(a, stream, info);
+    if (a.G == 64 && a.R == 2) return launch_instance<Ar, 64, 2, FEAT>(a, stream, info);
+    if (a.G == 64 && a.R == 4) return launch_instance<Ar, 64, 4, FEAT>(a, stream, info);
+    if (a.G == 128 && a.R == 2) return launch_instance<Ar, 128, 2, FEAT>(a, stream, info);
+    if (a.G == 128 && a.R == 4) return launch_instance<Ar, 128, 4, FEAT>(a, stream, info);
+    if (a.G == 256 && a.R == 2) return launch_instance<Ar, 256, 2, FEAT>(a, stream, info);
+    if (a.G == 256 && a.R == 4) return launch_instance<Ar, 256, 4, FEAT>(a, stream, info);
     return cudaErrorInvalidValue;
 }
 

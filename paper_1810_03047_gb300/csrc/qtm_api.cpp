@@ -68,6 +68,8 @@ struct qtm_ctx {
     std::vector<cd> psi0;
     Csr M;                       // host copies of the operators, for repacking
     std::vector<Csr> Cops, Aops;
+    std::vector<Csr> Dops;       // -i H_k of the time-dependent terms
+    std::vector<double> drive;   // 3 per term: a_k, omega_k, phi_k
     DevBuf d_ints, d_vals, d_t, d_psi0, d_queue, d_counters, d_first_error;
     DevBuf d_out, d_partial, d_stats, d_njumps, d_jump_t, d_jump_ch;
     // learned jump-time proposal
@@ -308,6 +310,7 @@ void repack(qtm_ctx *ctx, qtm::Layout lay)
     pack(ctx, ctx->M, lay);
     for (const Csr &c : ctx->Cops) pack(ctx, c, lay);
     for (const Csr &a : ctx->Aops) pack(ctx, a, lay);
+    for (const Csr &d : ctx->Dops) pack(ctx, d, lay);
 }
 
 // Real values in the layout of the kernel's arithmetic: doubles for complex128,
@@ -786,6 +789,10 @@ static qtm_status enqueue_run(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64
         a.n_jumps = (int *)ctx->d_njumps.p;
         a.jump_t = (double *)ctx->d_jump_t.p;
         a.jump_ch = (int *)ctx->d_jump_ch.p;
+        a.n_drive = (int)ctx->Dops.size();
+        a.drive_op0 = 1 + ctx->n_c + ctx->n_obs;
+        for (int k = 0; k < a.n_drive; ++k)
+            for (int q = 0; q < 3; ++q) a.drive[k][q] = ctx->drive[3 * k + q];
         a.rec_stride = ctx->rec_stride;
         a.rec_max = ctx->rec_max;
         a.rec = (float *)ctx->d_rec.p;
@@ -812,7 +819,13 @@ static qtm_status enqueue_run(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64
         if (prop && (ctx->precision == QTM_PREC_C64 || ctx->layout.G > 32))
             return fail(ctx, QTM_ERR_UNSUPPORTED,
                         "qtm_run: the learned proposal needs complex128 or double-float and dimension <= 64");
-        if (ctx->precision == QTM_PREC_DF64)
+        if (prop && a.n_drive > 0)
+            return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_run: the learned proposal takes a constant Hamiltonian");
+        if (a.n_drive > 0)
+            e = ctx->precision == QTM_PREC_DF64  ? qtm::launch_mcwf_df64_drive(a, s, &ctx->info)
+              : ctx->precision == QTM_PREC_C64   ? qtm::launch_mcwf_c64_drive(a, s, &ctx->info)
+                                                 : qtm::launch_mcwf_c128_drive(a, s, &ctx->info);
+        else if (ctx->precision == QTM_PREC_DF64)
             e = prop ? qtm::launch_mcwf_df64_prop(a, s, &ctx->info) : qtm::launch_mcwf_df64(a, s, &ctx->info);
         else if (ctx->precision == QTM_PREC_C64)
             e = qtm::launch_mcwf_c64(a, s, &ctx->info);
@@ -1383,6 +1396,46 @@ qtm_status qtm_mlp_loss_grad(const float *params, const float *x, const float *t
         e = cudaMemcpy(loss, dloss, sizeof(float), cudaMemcpyDeviceToHost);
     cudaFree(d);
     return e ? cuda_fail(nullptr, e, "qtm_mlp_loss_grad") : QTM_OK;
+}
+
+qtm_status qtm_set_drive(qtm_ctx *ctx, int32_t n_terms, const qtm_op *H, const double *coef)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_set_drive: ctx is NULL");
+    ctx->err.clear();
+    if (n_terms < 0 || n_terms > qtm::kMaxDrive) {
+        char buf[96];
+        std::snprintf(buf, sizeof buf, "qtm_set_drive: n_terms must be in [0, %d]", qtm::kMaxDrive);
+        return fail(ctx, QTM_ERR_ARG, buf);
+    }
+    if (n_terms > 0 && (!H || !coef)) return fail(ctx, QTM_ERR_ARG, "qtm_set_drive: H or coef is NULL");
+    if (n_terms > 0 && ctx->precision == QTM_PREC_BF16X6)
+        return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_set_drive: the tensor-core path has a constant operator");
+    if (1 + ctx->n_c + ctx->n_obs + n_terms > qtm::kMaxOps)
+        return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_set_drive: too many operators in total");
+    std::vector<Csr> D(n_terms);
+    for (int k = 0; k < n_terms; ++k) {
+        char name[32];
+        std::snprintf(name, sizeof name, "drive H[%d]", k);
+        qtm_status st = read_op(H[k], ctx->n, name, D[k]);
+        if (st) {
+            ctx->err = g_create_error;
+            return st;
+        }
+        if (!is_hermitian(D[k])) {
+            std::snprintf(name, sizeof name, "qtm_set_drive: H[%d] is not Hermitian", k);
+            return fail(ctx, QTM_ERR_ARG, name);
+        }
+        for (int q = 0; q < 3; ++q)
+            if (!is_finite(coef[3 * k + q])) return fail(ctx, QTM_ERR_ARG, "qtm_set_drive: non-finite coefficient");
+        for (cd &v : D[k].val) v *= cd(0.0, -1.0);  // -i H_k
+    }
+    ctx->Dops = std::move(D);
+    ctx->drive.assign(coef, coef + 3 * (size_t)n_terms);
+    repack(ctx, ctx->layout);
+    qtm_status st = upload_ops(ctx);
+    if (st) return st;
+    ctx->last_ntraj = -1;
+    return QTM_OK;
 }
 
 qtm_status qtm_rhs_batch(qtm_ctx *ctx, int64_t n_vec, const double *y, double *my)

@@ -127,6 +127,12 @@ struct DP5 {
         return j == 0 ? 35.0 / 384.0 : j == 2 ? 500.0 / 1113.0 : j == 3 ? 125.0 / 192.0
              : j == 4 ? -2187.0 / 6784.0 : j == 5 ? 11.0 / 84.0 : 0.0;
     }
+    // nodes: stage s is evaluated at t + c_s h (c_s = sum_j a_sj)
+    __host__ __device__ static constexpr double c(int s)
+    {
+        return s == 1 ? 1.0 / 5.0 : s == 2 ? 3.0 / 10.0 : s == 3 ? 4.0 / 5.0 : s == 4 ? 8.0 / 9.0
+             : (s == 5 || s == 6) ? 1.0 : 0.0;
+    }
     // embedded 4th-order weights
     __host__ __device__ static constexpr double bhat(int j)
     {

@@ -7,7 +7,8 @@
 
 namespace qtm {
 
-constexpr int kMaxOps = 64;        // M + collapse operators + observables
+constexpr int kMaxOps = 64;        // M + collapse operators + observables + drive terms
+constexpr int kMaxDrive = 8;       // time-dependent terms a_k cos(omega_k t + phi_k) H_k
 constexpr int kMaxChannels = 48;   // collapse operators per problem
 
 // One operator inside the packed operator blob.  Its real and imaginary parts are
@@ -95,6 +96,10 @@ struct KernelArgs {
     const float *mlp;         // proposal network (weights and feature normalisation) or null
     float prop_margin;        // a proposed step ends this fraction past the predicted crossing
     int smem_ybuf_offset;     // byte offset of the per-trajectory vector slots
+    // time-dependent Hamiltonian: op[drive_op0 + k] = -i H_k, coefficient
+    // a_k cos(omega_k t + phi_k) with drive[k] = {a_k, omega_k, phi_k}
+    int n_drive, drive_op0;
+    double drive[kMaxDrive][3];
 };
 
 enum CounterIndex { kAccepted = 0, kRejected, kRhs, kJumps, kRootIters, kFailed, kNumCounters };
@@ -121,6 +126,10 @@ cudaError_t launch_mcwf_c64_large(const KernelArgs &args, cudaStream_t stream, L
 // Instantiations with the learned proposal compiled in (single-warp layouts only).
 cudaError_t launch_mcwf_c128_prop(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
 cudaError_t launch_mcwf_df64_prop(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+// Instantiations with the time-dependent terms compiled in (every lane layout).
+cudaError_t launch_mcwf_c128_drive(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+cudaError_t launch_mcwf_df64_drive(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+cudaError_t launch_mcwf_c64_drive(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
 inline cudaError_t launch_mcwf_c128(const KernelArgs &a, cudaStream_t s, LaunchInfo *i)
 {
     return a.G <= 32 ? launch_mcwf_c128_small(a, s, i) : launch_mcwf_c128_large(a, s, i);

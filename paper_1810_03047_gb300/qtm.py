@@ -14,6 +14,7 @@ import threading
 from typing import Optional
 
 import numpy as np
+import scipy.sparse as sp
 
 from . import build as _build
 
@@ -44,7 +45,7 @@ EXPORTS = ["qtm_set_allocator", "qtm_create", "qtm_run", "qtm_run_range", "qtm_e
            "qtm_destroy", "qtm_version", "qtm_ensemble_reduce_static", "qtm_run_batch", "qtm_autotune",
            "qtm_set_layout", "qtm_proposal_collect", "qtm_proposal_pairs", "qtm_proposal_train",
            "qtm_proposal_set", "qtm_proposal_get", "qtm_proposal_enable", "qtm_mlp_loss_grad",
-           "qtm_rhs_batch"]
+           "qtm_rhs_batch", "qtm_set_drive"]
 
 QTM_PROPOSAL_FLOATS = 4685
 MLP_PARAMS = 4673
@@ -135,6 +136,8 @@ def lib():
             dp = ct.POINTER(ct.c_double)
             L.qtm_rhs_batch.argtypes = [ct.c_void_p, ct.c_int64, dp, dp]
             L.qtm_rhs_batch.restype = ct.c_int
+            L.qtm_set_drive.argtypes = [ct.c_void_p, ct.c_int32, ct.POINTER(QtmOp), dp]
+            L.qtm_set_drive.restype = ct.c_int
             for name in ("qtm_proposal_collect", "qtm_proposal_pairs", "qtm_proposal_train", "qtm_proposal_set",
                          "qtm_proposal_get", "qtm_proposal_enable", "qtm_mlp_loss_grad"):
                 getattr(L, name).restype = ct.c_int
@@ -275,7 +278,15 @@ def qtm_create(prob, stream=None, precision: int = QTM_PREC_C128, record_jumps: 
     p, keep = make_problem(prob, precision, record_jumps)
     h = ct.c_void_p()
     _check(lib().qtm_create(ct.byref(p), ct.c_void_p(stream or 0), ct.byref(h)))
-    return Ctx(h.value, len(prob.t), len(prob.A), int(record_jumps))
+    ctx = Ctx(h.value, len(prob.t), len(prob.A), int(record_jumps))
+    drive = list(getattr(prob, "drive", []) or [])
+    if drive:
+        try:
+            qtm_set_drive(ctx, drive)
+        except QtmError:
+            qtm_destroy(ctx)
+            raise
+    return ctx
 
 
 def qtm_run(ctx: Ctx, ntraj: int, seed: int):
@@ -427,6 +438,25 @@ def qtm_ensemble_reduce_static(values_dev: int, ntraj: int, n_values: int, sum_d
                                             ct.c_void_p(sum_dev), ct.c_void_p(sumsq_dev),
                                             ct.c_void_p(mean_dev), ct.c_void_p(stderr_dev),
                                             ct.c_void_p(stream or 0)))
+
+
+def qtm_set_drive(ctx: Ctx, terms):
+    """Time-dependent terms [(H_k, a_k, omega_k, phi_k), ...]: H(t) = H + sum a_k cos(omega_k t + phi_k) H_k."""
+    keep = []
+    ops = []
+    for Hk, _, _, _ in terms:
+        m = sp.csr_matrix(Hk)
+        rp = np.ascontiguousarray(m.indptr, dtype=np.int32)
+        ci = np.ascontiguousarray(m.indices, dtype=np.int32)
+        v = np.ascontiguousarray(m.data, dtype=np.complex128).view(np.float64)
+        keep += [rp, ci, v]
+        ops.append(QtmOp(int(m.shape[0]), QTM_FORMAT_CSR, rp.ctypes.data_as(ct.POINTER(ct.c_int32)),
+                         ci.ctypes.data_as(ct.POINTER(ct.c_int32)), v.ctypes.data_as(ct.POINTER(ct.c_double)),
+                         int(m.nnz)))
+    arr = (QtmOp * max(1, len(ops)))(*ops)
+    coef = np.ascontiguousarray([[float(a), float(w), float(ph)] for _, a, w, ph in terms] or [[0.0, 0.0, 0.0]],
+                                dtype=np.float64)
+    _check(lib().qtm_set_drive(ctx.handle, len(ops), arr, coef.ctypes.data_as(ct.POINTER(ct.c_double))), ctx)
 
 
 def qtm_rhs_batch(ctx: Ctx, y) -> np.ndarray:
