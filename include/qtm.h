@@ -73,7 +73,7 @@ typedef enum {
     QTM_ERR_STEPSIZE = 5,     /* step size fell below 1e-14 max(1, |t|) */
     QTM_ERR_NONFINITE = 6,    /* a non-finite error norm (NaN/Inf state) */
     QTM_ERR_NO_CHANNEL = 7,   /* the norm fell to r but every ||C_n psi|| was 0 */
-    QTM_ERR_TIMEOUT = 8,      /* a bounded device wait of the tensor-core engine gave up */
+    QTM_ERR_TIMEOUT = 8,      /* a bounded device wait of the tensor-core engine gave up (qtm_set_wait_limit) */
     QTM_ERR_STATE = 9,        /* call out of order (e.g. qtm_expect before qtm_run) */
     QTM_ERR_UNSUPPORTED = 10  /* the problem has no kernel in this build (e.g. dim too large) */
 } qtm_status;
@@ -347,6 +347,15 @@ const char *qtm_status_string(qtm_status status);
  * runs; QTM_ERR_UNSUPPORTED for QTM_PREC_BF16X6 (its operator is constant) or
  * when the operators no longer fit a kernel (reported by qtm_run). */
 qtm_status qtm_set_drive(qtm_ctx *ctx, int32_t n_terms, const qtm_op *H, const double *coef);
+
+/* Bound (nanoseconds of wall clock) on any single device-side wait of the
+ * tensor-core engine (QTM_PREC_BF16X6: its producer, tensor-core and TMA roles
+ * hand tiles to one another through shared-memory barriers).  A wait that runs
+ * past it ends the launch: every role winds down, the engine's device state is
+ * released, and the next synchronising call returns QTM_ERR_TIMEOUT; the context
+ * stays usable.  0 restores the default (2 s).  No effect on the other
+ * arithmetics (their kernels have no cross-role waits). */
+qtm_status qtm_set_wait_limit(qtm_ctx *ctx, uint64_t limit_ns);
 
 /* Batched right-hand side: my[v] = M y[v] with M = -i H_eff, for n_vec vectors
  * y (HOST, [n_vec][dim] complex, interleaved (re, im) doubles; rounded to FP32)

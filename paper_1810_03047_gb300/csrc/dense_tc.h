@@ -58,6 +58,7 @@ struct DenseArgs {
     float *state;          // [kNumDenseVecs][cols][2 np]
     DenseCol *col;         // [cols]
     int mode;              // DenseMode
+    unsigned long long wait_limit_ns;  // bound of one device wait (0: 2 s); past it the run reports QTM_ERR_TIMEOUT
     const float *rhs_in;   // rhs mode: [rhs_n][2 np] vectors (planar as the state)
     float *rhs_out;        // rhs mode: [rhs_n][2 np] = M in
     long long rhs_n;

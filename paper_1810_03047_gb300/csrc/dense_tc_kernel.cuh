@@ -120,6 +120,7 @@ struct Pipe {
     unsigned char *op, *yt;
     uint64_t *op_full, *op_empty, *y_full, *y_empty, *acc_full;
     volatile int *abort;
+    unsigned long long limit;   // wall-clock bound of one wait (ns)
     uint32_t tmem;
     uint32_t ocnt, ycnt, acnt;  // ring positions (every role advances its own copy identically)
 };
@@ -138,7 +139,7 @@ __device__ void role_tma(const DenseArgs &a, Pipe &p, const CUtensorMap *map)
         for (int split = 0; split < kSplits; ++split)
             for (int c = 0; c < S::NCHUNK; ++c) {
                 const uint32_t slot = p.ocnt % kOpRing, ph = (p.ocnt / kOpRing) & 1;
-                if (!tc::mbar_wait(&p.op_empty[slot], ph ^ 1, p.abort)) {
+                if (!tc::mbar_wait(&p.op_empty[slot], ph ^ 1, p.abort, p.limit)) {
                     raise_abort(a, p);
                     return;
                 }
@@ -159,7 +160,7 @@ __device__ void role_mma(const DenseArgs &a, Pipe &p)
     using S = TcShape<NP>;
     for (int kb = 0; kb < S::NKB; ++kb) {
         const uint32_t ys = p.ycnt & 1, yph = (p.ycnt >> 1) & 1;
-        if (!tc::mbar_wait(&p.y_full[ys], yph, p.abort)) {
+        if (!tc::mbar_wait(&p.y_full[ys], yph, p.abort, p.limit)) {
             raise_abort(a, p);
             return;
         }
@@ -168,7 +169,7 @@ __device__ void role_mma(const DenseArgs &a, Pipe &p)
         for (int split = 0; split < kSplits; ++split)
             for (int c = 0; c < S::NCHUNK; ++c) {
                 const uint32_t os = p.ocnt % kOpRing, oph = (p.ocnt / kOpRing) & 1;
-                if (!tc::mbar_wait(&p.op_full[os], oph, p.abort)) {
+                if (!tc::mbar_wait(&p.op_full[os], oph, p.abort, p.limit)) {
                     raise_abort(a, p);
                     return;
                 }
@@ -255,7 +256,7 @@ __device__ void role_producer(const DenseArgs &a, Pipe &p, int s, long long tile
     const int kk = (lane & 15) * 4;  // this thread's 4 values within the 64-wide k-block
     for (int kb = 0; kb < S::NKB; ++kb) {
         const uint32_t ys = p.ycnt & 1, yph = (p.ycnt >> 1) & 1;
-        if (!tc::mbar_wait(&p.y_empty[ys], yph ^ 1, p.abort)) {
+        if (!tc::mbar_wait(&p.y_empty[ys], yph ^ 1, p.abort, p.limit)) {
             raise_abort(a, p);
             return;
         }
@@ -278,7 +279,7 @@ __device__ void role_producer(const DenseArgs &a, Pipe &p, int s, long long tile
     // epilogue: tensor memory -> K_s
     const uint32_t aph = p.acnt & 1;
     ++p.acnt;
-    if (!tc::mbar_wait(p.acc_full, aph, p.abort)) {
+    if (!tc::mbar_wait(p.acc_full, aph, p.abort, p.limit)) {
         raise_abort(a, p);
         return;
     }
@@ -974,6 +975,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     p.abort = s_abort;
     p.tmem = *s_tmem;
     p.ocnt = p.ycnt = p.acnt = 0;
+    p.limit = a.wait_limit_ns ? a.wait_limit_ns : tc::kWaitLimitNs;
 
     if (a.mode == kDenseRhs) {
         const long long tiles = (a.rhs_n + kTcCols - 1) / kTcCols;
@@ -1026,8 +1028,14 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         }
     }
 
-    // drain: every tensor-core operation of this CTA has completed before the
-    // tensor memory is released
+    // drain: the operator loads this CTA issued have landed (after an abort some
+    // may not have been consumed), and every tensor-core operation has completed
+    // before the tensor memory is released
+    if (warp == 0 && lane == 0) {
+        int no_abort = 0;
+        for (uint32_t i = p.ocnt > (uint32_t)kOpRing ? p.ocnt - kOpRing : 0; i < p.ocnt; ++i)
+            tc::mbar_wait(&p.op_full[i % kOpRing], (i / kOpRing) & 1, &no_abort);
+    }
     __syncthreads();
     if (warp == 1) {
         if (lane == 0) {

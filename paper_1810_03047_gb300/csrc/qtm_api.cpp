@@ -82,6 +82,7 @@ struct qtm_ctx {
     // tensor-core engine (QTM_PREC_BF16X6): bf16 operator splits, their tensor
     // map, the column state and per-column records
     int np = 0, sms = 0;
+    unsigned long long wait_limit_ns = 0;  // 0: the engine's default bound
     DevBuf d_op, d_state, d_col, d_rhs, d_dense;
     std::vector<int> dense_off;  // per operator: float2 offset of its dense copy, -1 = SELL
     CUtensorMap op_map{};
@@ -808,6 +809,7 @@ static qtm_status enqueue_run(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64
             d.state = (float *)ctx->d_state.p;
             d.col = (qtm::DenseCol *)ctx->d_col.p;
             d.mode = qtm::kDenseRun;
+            d.wait_limit_ns = ctx->wait_limit_ns;
             d.dense = (const float2 *)ctx->d_dense.p;
             for (int i = 0; i < qtm::kMaxOps; ++i)
                 d.dense_off[i] = i < (int)ctx->dense_off.size() ? ctx->dense_off[i] : -1;
@@ -1438,6 +1440,14 @@ qtm_status qtm_set_drive(qtm_ctx *ctx, int32_t n_terms, const qtm_op *H, const d
     return QTM_OK;
 }
 
+qtm_status qtm_set_wait_limit(qtm_ctx *ctx, uint64_t limit_ns)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_set_wait_limit: ctx is NULL");
+    ctx->err.clear();
+    ctx->wait_limit_ns = limit_ns;
+    return QTM_OK;
+}
+
 qtm_status qtm_rhs_batch(qtm_ctx *ctx, int64_t n_vec, const double *y, double *my)
 {
     if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_rhs_batch: ctx is NULL");
@@ -1465,6 +1475,7 @@ qtm_status qtm_rhs_batch(qtm_ctx *ctx, int64_t n_vec, const double *y, double *m
     d.k.first_error = d_status;
     d.np = np;
     d.mode = qtm::kDenseRhs;
+    d.wait_limit_ns = ctx->wait_limit_ns;
     d.rhs_in = d_in;
     d.rhs_out = d_out;
     d.rhs_n = n_vec;

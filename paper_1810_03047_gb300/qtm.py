@@ -45,7 +45,7 @@ EXPORTS = ["qtm_set_allocator", "qtm_create", "qtm_run", "qtm_run_range", "qtm_e
            "qtm_destroy", "qtm_version", "qtm_ensemble_reduce_static", "qtm_run_batch", "qtm_autotune",
            "qtm_set_layout", "qtm_proposal_collect", "qtm_proposal_pairs", "qtm_proposal_train",
            "qtm_proposal_set", "qtm_proposal_get", "qtm_proposal_enable", "qtm_mlp_loss_grad",
-           "qtm_rhs_batch", "qtm_set_drive"]
+           "qtm_rhs_batch", "qtm_set_drive", "qtm_set_wait_limit"]
 
 QTM_PROPOSAL_FLOATS = 4685
 MLP_PARAMS = 4673
@@ -138,6 +138,8 @@ def lib():
             L.qtm_rhs_batch.restype = ct.c_int
             L.qtm_set_drive.argtypes = [ct.c_void_p, ct.c_int32, ct.POINTER(QtmOp), dp]
             L.qtm_set_drive.restype = ct.c_int
+            L.qtm_set_wait_limit.argtypes = [ct.c_void_p, ct.c_uint64]
+            L.qtm_set_wait_limit.restype = ct.c_int
             for name in ("qtm_proposal_collect", "qtm_proposal_pairs", "qtm_proposal_train", "qtm_proposal_set",
                          "qtm_proposal_get", "qtm_proposal_enable", "qtm_mlp_loss_grad"):
                 getattr(L, name).restype = ct.c_int
@@ -457,6 +459,11 @@ def qtm_set_drive(ctx: Ctx, terms):
     coef = np.ascontiguousarray([[float(a), float(w), float(ph)] for _, a, w, ph in terms] or [[0.0, 0.0, 0.0]],
                                 dtype=np.float64)
     _check(lib().qtm_set_drive(ctx.handle, len(ops), arr, coef.ctypes.data_as(ct.POINTER(ct.c_double))), ctx)
+
+
+def qtm_set_wait_limit(ctx: Ctx, limit_ns: int):
+    """Bound of one device wait of the tensor-core engine (0: the default 2 s)."""
+    _check(lib().qtm_set_wait_limit(ctx.handle, int(limit_ns)), ctx)
 
 
 def qtm_rhs_batch(ctx: Ctx, y) -> np.ndarray:

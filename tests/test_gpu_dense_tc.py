@@ -179,3 +179,28 @@ def test_full_size_dense_sample_against_complex128():
     d = np.abs(a["mean"] - b["mean"])
     assert d.max() <= 1e-3, d.max()
     assert b["stats"]["failed"] == 0
+
+
+def test_bounded_wait_reports_timeout_and_context_recovers():
+    """Failure detection without a fault: a 1 ns bound makes the first wait that is
+    not already satisfied give up; the launch winds down (operator loads in flight
+    land, tensor memory is released) and reports QTM_ERR_TIMEOUT.  The same
+    context then runs normally with the default bound and reproduces a fresh run."""
+    prob = S.dense_random(N=64, ntraj=200)
+    ref = gpu_run(prob, 200, precision=TC, record=0)
+    ctx = Q.qtm_create(prob, precision=TC)
+    Q.qtm_set_wait_limit(ctx, 1)
+    Q.qtm_run(ctx, 200, prob.seed)
+    with pytest.raises(Q.QtmError) as ei:
+        Q.qtm_expect(ctx)
+    assert ei.value.status == Q.QTM_ERR_TIMEOUT
+    Q.qtm_set_wait_limit(ctx, 0)
+    Q.qtm_run(ctx, 200, prob.seed)
+    np.testing.assert_array_equal(Q.qtm_traj_expect(ctx), ref["obs"])
+    with pytest.raises(Q.QtmError) as ei:
+        Q.qtm_set_wait_limit(ctx, 1)
+        Q.qtm_rhs_batch(ctx, np.ones((5, prob.dim), complex))
+    assert ei.value.status == Q.QTM_ERR_TIMEOUT
+    Q.qtm_set_wait_limit(ctx, 0)
+    assert np.all(np.isfinite(Q.qtm_rhs_batch(ctx, np.ones((5, prob.dim), complex))))
+    Q.qtm_destroy(ctx)
