@@ -34,7 +34,8 @@ struct DenseCol {
     int sel;                    // bit 0: psi in buffer 1 (else 0); bit 1: K_0 in slot 6 (else 0)
     int flags;                  // bit 0: previous attempt rejected; bit 1: this step ends at t_end
     int root_iters;
-    int pad[6];
+    int round;                  // trajectories this column has taken (static assignment)
+    int pad[5];
 };
 static_assert(sizeof(DenseCol) == 128, "DenseCol is 128 bytes");
 

@@ -735,21 +735,29 @@ struct ColCtl {
         return true;
     }
 
-    // Takes trajectories from the device counter until one is ready to integrate
-    // or none is left: (A), output 0, K_0 = M psi0 and the starting step.
+    // Takes the column's next trajectories until one is ready to integrate or none
+    // is left: (A), output 0, K_0 = M psi0 and the starting step.  The assignment
+    // is static -- the column at position j of CTA b runs trajectories
+    // b + G (j + 128 n), n = 0, 1, ..., for a grid of G CTAs -- so a CTA's work,
+    // and with it every result, is reproducible bitwise from run to run.  Position
+    // j = 8 u + w for the column u of control warp w spreads a CTA's last,
+    // partial round over its control warps.
     __device__ __noinline__ void refill(DenseCol &d) const
     {
         const double t_end = k.t[k.n_t - 1];
+        const long long b = blockIdx.x, G = gridDim.x, slot = c.col - b * kTcCols;
+        const long long jpos = (slot % 16) * 8 + slot / 16;
         for (;;) {
-            unsigned long long i = 0;
-            if (lane == 0) i = atomicAdd(k.queue, 1ULL);
-            i = __shfl_sync(0xffffffffu, i, 0);
-            if ((long long)i >= k.ntraj) {
+            const int n = d.round;
+            const long long i = b + G * (jpos + (long long)kTcCols * n);
+            if (i >= k.ntraj) {
                 d.il = -1;
+                d.round = n + 1;
                 return;
             }
             d = DenseCol{};
-            d.il = (long long)i;
+            d.round = n + 1;
+            d.il = i;
             jump_draws(k.seed, k.traj0 + d.il, 0, d.r, d.c);
             d.t = k.t[0];
             // psi0 into buffer 0 (padded rows zero) and scr
@@ -820,6 +828,49 @@ struct ColCtl {
     }
 
     // After the six products of an attempt.
+    // Tail mode: the six stage products of one attempt on this warp alone, with
+    // the control's own operator copy (FP32 products), leaving K_1..K_6 and ynew
+    // where the tensor-core stages put them.
+    __device__ __noinline__ void simt_products(const DenseCol &d) const
+    {
+        const float hf = (float)d.h;
+        const int pv = d.sel & 1, k0 = (d.sel & 2) ? 6 : 0;
+        float *yn = c.vec(1 - pv);
+        for (int s = 1; s <= 6; ++s) {
+            for (int r = 0; r < R; ++r) {
+                const int m = lane + 32 * r;
+                if (m >= k.n) continue;
+                float yr = re(pv, m), yi = im(pv, m);
+                for (int q = 0; q < s; ++q) {
+                    const float w = hf * cf[7 * s + q];
+                    if (w == 0.f) continue;
+                    const int v = kVK0 + (q == 0 ? k0 : q);
+                    yr = fmaf(w, re(v, m), yr);
+                    yi = fmaf(w, im(v, m), yi);
+                }
+                scr[2 * m] = yr;
+                scr[2 * m + 1] = yi;
+                if (s == 6) {
+                    yn[m] = yr;
+                    yn[NP + m] = yi;
+                }
+            }
+            __syncwarp();
+            cf32 v[R];
+            opmv(0, v);
+            float *dst = c.vec(kVK0 + (s == 6 ? 6 - k0 : s));
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int m = lane + 32 * r;
+                if (m < k.n) {
+                    dst[m] = v[r].re;
+                    dst[NP + m] = v[r].im;
+                }
+            }
+            __syncwarp();
+        }
+    }
+
     __device__ void step(DenseCol &d) const
     {
         const double t_end = k.t[k.n_t - 1];
@@ -935,6 +986,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(sm + S::OFF_MISC);
     int *s_abort = reinterpret_cast<int *>(sm + S::OFF_MISC + 4);
     int *s_count = reinterpret_cast<int *>(sm + S::OFF_MISC + 8);  // active columns per control warp
+    int *s_mode = reinterpret_cast<int *>(sm + S::OFF_MISC + 40);  // next attempt: 0 products, 1 tail, 2 done
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     for (int i = threadIdx.x; i < kCoefFloats; i += kThreadsTc) {
@@ -990,7 +1042,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
             int active = 0;
             for (int r = 16 * pw; r < 16 * pw + 16; ++r) {
                 cc.c.col = (int)(tile_base + r);
-                DenseCol d;
+                DenseCol d{};
                 cc.refill(d);
                 if (lane == 0) a.col[cc.c.col] = d;
                 s_hf[r] = d.il >= 0 ? (float)d.h : 0.f;
@@ -1001,9 +1053,40 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
         }
         __syncthreads();
         for (;;) {
-            int active = 0;
-            for (int w = 0; w < 8; ++w) active += s_count[w];
-            if (active == 0 || *s_abort) break;
+            // one thread decides the mode: with at most one live column per
+            // control warp, full 128-column products would mostly multiply idle
+            // columns, so the control warps finish their columns alone (the
+            // decision depends only on this CTA's columns, so it is reproducible)
+            if (threadIdx.x == 0) {
+                int active = 0;
+                for (int w = 0; w < 8; ++w) active += s_count[w];
+                *s_mode = (active == 0 || *s_abort) ? 2 : active <= 8 ? 1 : 0;
+            }
+            __syncthreads();
+            const int mode = *s_mode;
+            if (mode == 2) break;
+            if (mode == 1) {
+                if (warp >= 2) {
+                    const int pw = warp - 2;
+                    ColCtl<NP> cc{a, a.k, Group<32>(threadIdx.x, nullptr), lane, Ctl{&a, 0, NP, S::KD},
+                                  scr_all + pw * S::KD, cf};
+                    int act = 0;
+                    for (int r = 16 * pw; r < 16 * pw + 16; ++r) {
+                        cc.c.col = (int)(tile_base + r);
+                        DenseCol d = a.col[cc.c.col];
+                        if (d.il >= 0) {
+                            cc.simt_products(d);
+                            cc.step(d);
+                            __syncwarp();
+                            if (lane == 0) a.col[cc.c.col] = d;
+                        }
+                        act += d.il >= 0;
+                    }
+                    if (lane == 0) s_count[pw] = act;
+                }
+                __syncthreads();
+                continue;
+            }
             for (int s = 1; s <= 6; ++s) stage_product<NP>(a, p, &opmap, s, tile_base, s_hf, s_sel, cf);
             if (warp >= 2 && !*s_abort) {
                 const int pw = warp - 2;
