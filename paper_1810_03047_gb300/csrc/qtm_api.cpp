@@ -662,6 +662,16 @@ qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
     // the tensor-core engine's control warps use one lane per row group of 32
     repack(ctx, p->precision == QTM_PREC_BF16X6 ? qtm::Layout{32, qtm::tc_padded_dim(n) / 32}
                                                 : qtm::layout_for_dim(n));
+    if (p->precision != QTM_PREC_BF16X6 && ctx->layout.G <= 32) {
+        // single-warp layouts keep the operators in shared memory beside four
+        // trajectories' ten vector slots; operators that cannot fit there (dense
+        // ones) go to the 64-lane layout, whose kernels read them from L2
+        const size_t real_b = p->precision == QTM_PREC_C64 ? 4 : 8;
+        const size_t cplx_b = p->precision == QTM_PREC_C64 ? 8 : 16;
+        const size_t need = ctx->ints.size() * 4 + ctx->reals.size() * real_b +
+                            4 * 10 * (size_t)ctx->layout.G * ctx->layout.R * cplx_b + 4096;
+        if (need > 220 * 1024) repack(ctx, qtm::Layout{64, 2});
+    }
 
     cudaError_t e = cudaGetDevice(&ctx->device);
     if (e != cudaSuccess) {

@@ -143,6 +143,19 @@ def test_ragged_and_tiny_ensembles(orc, ntraj):
     assert np.all(np.isfinite(g["obs"]))
 
 
+@pytest.mark.parametrize("prec", [Q.QTM_PREC_C128, Q.QTM_PREC_DF64])
+def test_dense_small_system_on_the_simt_paths(orc, prec):
+    """Dense N = 64 operators do not fit the single-warp layouts' shared memory;
+    the library then takes the 64-lane layout (operators read from L2) and the
+    FP64-class paths meet the usual trajectory-by-trajectory bars."""
+    from test_gpu_parity import compare
+    prob = S.dense_random(N=64, ntraj=40)
+    g = gpu_run(prob, 40, precision=prec)
+    o = oracle_run(orc, prob, 40)
+    compare(g, o, 40, precision=prec)
+    assert g["stats"]["kernel_group"] == 64
+
+
 def test_refill_beyond_the_resident_columns():
     """More trajectories than resident columns (152 CTAs x 128): finished columns
     take new trajectory ids from the device counter.  Checked against the
