@@ -34,7 +34,7 @@ __all__ = [
     "Problem", "destroy", "sigma_minus", "sigma_z", "sigma_x", "sigma_y", "kron",
     "two_level_driven", "jaynes_cummings_driven", "dense_random", "ising_chain",
     "ising_batch", "learned_proposal_system", "paper_unitary", "paper_trilinear",
-    "paper_jaynes_cummings", "paper_photon_birth_death", "fock_decay", "by_name",
+    "paper_jaynes_cummings", "paper_photon_birth_death", "fock_decay", "purcell_qubit", "by_name",
 ]
 
 
@@ -346,6 +346,27 @@ def fock_decay(n0: int = 3, n_fock: int = 6, kappa: float = 0.5, omega: float = 
                    ntraj, seed, obs_names=["a^dag a"])
 
 
+def purcell_qubit(ntraj: int = 2000, seed: int = 1, n_fock: int = 5, g: float = 5.0, kappa: float = 200.0,
+                  gamma: float = 0.05, omega: float = 0.5, n_t: int = 201, t_end: float = 20.0) -> Problem:
+    """A stiff system: a driven qubit coupled to a strongly damped cavity (Purcell regime).
+
+    a = d_N (x) I_2, b = I_N (x) sigma_-, H = g (a^dag b + a b^dag) + (omega / 2)(b + b^dag),
+    C = {sqrt(kappa) a, sqrt(gamma) b}, psi0 = |0> (x) |e>, observables b^dag b and a^dag a.
+    The cavity decays at kappa = 200 while the qubit relaxes through it at the Purcell
+    rate 4 g^2 / kappa = 0.5: the rates of H_eff span more than two decades, so an
+    explicit integrator's step is set by stability (h ~ 3.3 / (kappa n / 2)) rather
+    than by accuracy (the setting of Sec. 2.1 where the paper switches ZVODE to BDF).
+    """
+    a = kron(destroy(n_fock), eye(2))
+    b = kron(eye(n_fock), sigma_minus())
+    H = _csr(g * (dag(a) @ b + a @ dag(b)) + 0.5 * omega * (b + dag(b)))
+    C = [_csr(math.sqrt(kappa) * a), _csr(math.sqrt(gamma) * b)]
+    A = [_csr(dag(b) @ b), _csr(dag(a) @ a)]
+    psi0 = np.kron(basis(n_fock, 0), basis(2, 0))
+    return Problem("purcell_qubit", H, C, A, psi0, np.linspace(0.0, t_end, n_t), 1e-8, 1e-10, ntraj, seed,
+                   obs_names=["b^dag b", "a^dag a"])
+
+
 def by_name(name: str, **kw) -> Problem:
     table = {
         "two_level_driven": two_level_driven,
@@ -359,6 +380,7 @@ def by_name(name: str, **kw) -> Problem:
         "fock_decay": fock_decay,
         "driven_dephasing_qubit": driven_dephasing_qubit,
         "jaynes_cummings_pulsed": jaynes_cummings_pulsed,
+        "purcell_qubit": purcell_qubit,
     }
     if name.startswith("ising_L"):
         return ising_chain(int(name[len("ising_L"):]), **kw)
