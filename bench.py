@@ -59,6 +59,8 @@ def parse():
                     help="skip the dense tensor-core measurement (N = 256, 20,000 trajectories)")
     ap.add_argument("--no-proposal", action="store_true",
                     help="skip the learned jump-time proposal measurement (200,000 JC trajectories)")
+    ap.add_argument("--no-expo", action="store_true",
+                    help="skip the exponential-method legs (stiff Purcell system, Jaynes-Cummings)")
     ap.add_argument("--no-ising", action="store_true",
                     help="skip the batched Ising-chain measurement (L = 6..10 in one CUDA graph)")
     ap.add_argument("--only", choices=["c128", "df64", "c64", "dense"], default=None,
@@ -446,6 +448,9 @@ def main():
     if not args.no_dense:
         line["dense_tensor_core"] = dense_tensor_core(Q, torch, stream, world, rank, dist, pk)
         line["gpu_launches"] += line["dense_tensor_core"].pop("launches")
+    if not args.no_expo:
+        line["exponential_method"] = exponential_method(Q, torch, stream, world, rank, dist, pk, ref["mean"])
+        line["gpu_launches"] += line["exponential_method"].pop("launches")
     if not args.no_proposal:
         line["learned_proposal"] = learned_proposal(Q, torch, stream, world, rank, dist)
         line["gpu_launches"] += line["learned_proposal"].pop("launches")
@@ -620,6 +625,94 @@ def dense_tensor_core(Q, torch, stream, world, rank, dist, pk, ntraj=20000, samp
                          "frac": achieved / peak, "traffic": None, "kernel": "qtm::dense_tc_kernel<256>",
                          "bytes_per_attempt": bytes_per_attempt, "peak_note": note, "kernel_ms": kms},
             "launches": 3 * 5 + 5}
+
+
+def _timed_passes(Q, torch, stream, world, dist, prob, prec, method, first, count, passes=2):
+    """One warm-up and `passes` timed runs of one context (CUDA events on the
+    launching stream, max over ranks); returns throughput, time and counters."""
+    ctx = Q.qtm_create(prob, stream=int(stream.cuda_stream), precision=prec)
+    Q.qtm_set_method(ctx, method)
+    Q.qtm_run_range(ctx, first, count, prob.seed)
+    Q.qtm_expect(ctx)
+    ms = []
+    for _ in range(passes):
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Q.qtm_run_range(ctx, first, count, prob.seed)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = torch.tensor([max(ms)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    st = Q.qtm_stats(ctx)
+    mean = Q.qtm_expect(ctx)[0]
+    Q.qtm_destroy(ctx)
+    return {"value": world * count / (float(t.item()) / 1e3), "ms_per_step": float(t.item()),
+            "kernel_ms": st["kernel_ms"], "products_per_trajectory": st["rhs_evals"] / count,
+            "jumps_per_trajectory": st["jumps"] / count, "mean": mean, "launches": (1 + passes) * 5}
+
+
+def exponential_method(Q, torch, stream, world, rank, dist, pk, jc_ref_mean, ntraj=20000):
+    """The exponential method (exact propagation between jumps through a ladder of
+    precomputed exp(M delta 2^l); Sec. 2.1's stiff-problem setting) against the
+    Dormand-Prince path on the same trajectory ids: (1) the stiff Purcell system (a
+    driven qubit on a cavity with kappa = 200, Purcell rate 0.5, N = 10, 201
+    outputs on [0, 20]), where the explicit integrator's step is set by stability,
+    and (2) the headline Jaynes-Cummings workload (N = 60, 401 outputs on
+    [0, 40]), where it is not.  Observable errors are against the complex128
+    Dormand-Prince path.  Roofline of the exponential kernel on the
+    Jaynes-Cummings workload: per trajectory and output interval one dense
+    product P x (N^2 complex multiply-adds = 8 N^2 flops), against the FP64 peak
+    (complex128) or the double-float emulation peak."""
+    from paper_1810_03047_gb300 import shards
+    from paper_1810_03047_gb300 import systems as S
+    first, count = shards.shard(world * ntraj, world, rank)
+    D, E = Q.QTM_METHOD_DOPRI5, Q.QTM_METHOD_EXPONENTIAL
+    out, launches = {}, 0
+    stiff = S.purcell_qubit(ntraj=ntraj)
+    r = {}
+    for key, prec, meth in (("expo_df64", Q.QTM_PREC_DF64, E), ("expo_c128", Q.QTM_PREC_C128, E),
+                            ("dopri5_df64", Q.QTM_PREC_DF64, D), ("dopri5_c128", Q.QTM_PREC_C128, D)):
+        r[key] = _timed_passes(Q, torch, stream, world, dist, stiff, prec, meth, first, count)
+        launches += r[key].pop("launches")
+    ref = r["dopri5_c128"]["mean"]
+    out["stiff_purcell"] = {
+        "workload": "driven qubit + cavity (Purcell): N=10, g=5, kappa=200, gamma=0.05, drive 0.5, 201 outputs "
+                    f"on [0, 20], {world * count} trajectories (seed 1)",
+        "unit": UNIT,
+        **{k: {kk: vv for kk, vv in v.items() if kk != "mean"} for k, v in r.items()},
+        "speedup_expo_df64_vs_dopri5_df64": r["expo_df64"]["value"] / r["dopri5_df64"]["value"],
+        "speedup_expo_c128_vs_dopri5_c128": r["expo_c128"]["value"] / r["dopri5_c128"]["value"],
+        "observable_error_expo_c128_vs_dopri5_c128": float(np.abs(r["expo_c128"]["mean"] - ref).max()),
+        "observable_error_expo_df64_vs_dopri5_c128": float(np.abs(r["expo_df64"]["mean"] - ref).max()),
+    }
+    prob, _, _ = workload(ntraj)
+    j = {}
+    for key, prec in (("expo_df64", Q.QTM_PREC_DF64), ("expo_c128", Q.QTM_PREC_C128)):
+        j[key] = _timed_passes(Q, torch, stream, world, dist, prob, prec, E, first, count)
+        launches += j[key].pop("launches")
+    n = prob.dim
+    flops = 8.0 * n * n * (len(prob.t) - 1)  # the output-interval products, per trajectory
+    jc = {"workload": f"damped driven Jaynes-Cummings (N=60), 401 outputs on [0, 40], {world * count} trajectories",
+          "unit": UNIT}
+    for key, peak_key in (("expo_df64", "df64"), ("expo_c128", "c128")):
+        v = j[key]
+        achieved = flops * count / (v["kernel_ms"] / 1e3) / 1e12
+        peak, note = pk[peak_key]
+        jc[key] = {kk: vv for kk, vv in v.items() if kk != "mean"}
+        jc[key]["observable_error_vs_dopri5_c128"] = float(np.abs(v["mean"] - jc_ref_mean).max())
+        jc[key]["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                               "frac": achieved / peak, "traffic": None, "peak_note": note,
+                               "flops_note": "8 N^2 per trajectory and output interval (P_L x); the "
+                                             "observables, jumps and Taylor products are not counted"}
+    out["jaynes_cummings"] = jc
+    out["launches"] = launches
+    return out
 
 
 def learned_proposal(Q, torch, stream, world, rank, dist, ntraj=200000):

@@ -102,6 +102,13 @@ enum {
                            scalars.  No learned proposal, no layout choice */
 };
 
+/* Integrator of the no-jump evolution (qtm_set_method). */
+enum {
+    QTM_METHOD_DOPRI5 = 0,      /* Dormand-Prince 5(4) with error control and continuous extension (default) */
+    QTM_METHOD_EXPONENTIAL = 1  /* exact propagation psi(t) = exp(M (t - t_k)) psi_k between jumps, for stiff
+                                   problems; see qtm_set_method */
+};
+
 /* qtm_problem.flags */
 enum {
     QTM_FLAG_RECORD_JUMPS = 1  /* keep the first max_jumps_recorded jump times/channels per trajectory */
@@ -363,6 +370,55 @@ qtm_status qtm_set_wait_limit(qtm_ctx *ctx, uint64_t limit_ns);
  * QTM_ERR_UNSUPPORTED otherwise).  my: HOST, [n_vec][dim] complex.  Runs on the
  * context stream and synchronises it; leaves the results of qtm_run untouched. */
 qtm_status qtm_rhs_batch(qtm_ctx *ctx, int64_t n_vec, const double *y, double *my);
+
+/* ---------------------------------------------------------------------------
+ * Exponential propagation for stiff problems.  Sec. 2.1 of the paper lets the
+ * user switch ZVODE from Adams to BDF when the trajectory equations are stiff
+ * (rates of H_eff spread over decades, so that an explicit integrator's step is
+ * limited by stability, not accuracy).  With a constant Hamiltonian the no-jump
+ * evolution dpsi/dt = M psi (M = -i H_eff) has the exact solution
+ * psi(t) = exp(M (t - t_k)) psi_k, which this method applies instead of
+ * integrating:
+ *   - at qtm_set_method the library computes, in FP64 on the host, the ladder
+ *     P_l = exp(M delta 2^l), l = 0..L, by scaling and squaring (Taylor degree
+ *     12 at nu delta <= 1/16, nu = max(||M||_1, ||M||_inf)), with delta 2^L the
+ *     output spacing (uniform grids) or the largest output interval;
+ *   - a trajectory moves from output to output with one dense product P_L psi
+ *     (uniform grids) or with the binary digits of the interval in units of
+ *     delta plus a degree-9 Taylor remainder;
+ *   - the squared norm cannot increase (d||psi||^2/dt = -sum_n ||C_n psi||^2),
+ *     so a jump happened before t_j exactly when ||psi(t_j)||^2 < r (Algorithm 1
+ *     (B)); the crossing is then bracketed within delta by a binary descent over
+ *     the ladder and solved by Newton's method on the Taylor polynomial of
+ *     exp(s M) psi (to 1e-15 max(1, |t|));
+ *   - steps (C) and (D) are those of the default method.
+ * Results differ from the exact trajectory by rounding and the root tolerance
+ * only (rtol and atol are not used), at a cost that does not depend on the
+ * stiffness.  Counters (qtm_stats) under this method: accepted = propagations
+ * ending at an output or a jump, rejected = ladder levels that overshot a
+ * crossing, rhs_evals = matrix-vector products (ladder levels and M),
+ * root_iters = Newton iterations.
+ * ------------------------------------------------------------------------- */
+
+/* Selects the method of later runs.  QTM_METHOD_EXPONENTIAL computes and uploads
+ * the ladder (host FP64, O(L n^3 + 12 nnz(M) n) operations; (L + 1) n^2 complex
+ * values of device memory) and needs QTM_PREC_C128 or QTM_PREC_DF64, dimension
+ * <= 256 and no time-dependent terms (QTM_ERR_UNSUPPORTED otherwise; the learned
+ * proposal is refused by qtm_run).  QTM_METHOD_DOPRI5 restores the default.
+ * QTM_ERR_ARG for any other value. */
+qtm_status qtm_set_method(qtm_ctx *ctx, int32_t method);
+
+/* The exponential method's ladder: number of levels L + 1 and the base step
+ * delta (either pointer may be NULL).  QTM_ERR_STATE when the context does not
+ * use the exponential method. */
+qtm_status qtm_expo_ladder(const qtm_ctx *ctx, int32_t *levels, double *delta);
+
+/* exp(M dt) for the problem's M = -i H - (1/2) sum_n C_n^dag C_n (only dim, H,
+ * n_c and C are read; HOST pointers), dt >= 0, by the same scaling and squaring
+ * as the exponential method's ladder.  out: HOST, n x n complex, row-major,
+ * interleaved (re, im).  Needs no GPU; the message of an error is available
+ * from qtm_last_error(NULL). */
+qtm_status qtm_propagator(const qtm_problem *problem, double dt, double *out);
 
 /* Releases the context's device memory (after synchronising its stream). NULL is ignored. */
 void qtm_destroy(qtm_ctx *ctx);

@@ -1,0 +1,12 @@
+// mcwf_c128_expo.cu -- complex128 instantiations of the exponential-propagation
+// trajectory kernel (mcwf_expo.cuh) for every lane layout up to dimension 256.
+#include "mcwf_expo.cuh"
+
+namespace qtm {
+
+cudaError_t launch_mcwf_c128_expo(const KernelArgs &a, cudaStream_t stream, LaunchInfo *info)
+{
+    return launch_expo<ArF64>(a, stream, info);
+}
+
+}  // namespace qtm

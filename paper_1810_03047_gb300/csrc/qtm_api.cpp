@@ -86,6 +86,13 @@ struct qtm_ctx {
     DevBuf d_op, d_state, d_col, d_rhs, d_dense;
     std::vector<int> dense_off;  // per operator: float2 offset of its dense copy, -1 = SELL
     CUtensorMap op_map{};
+    // exponential propagation (qtm_set_method): the ladder exp(M delta 2^l),
+    // l < expo_levels, as [level][n][n] row-major complex (host copy)
+    int method = QTM_METHOD_DOPRI5;
+    std::vector<cd> ladder;
+    int expo_levels = 0, expo_uniform = 0;
+    double expo_delta = 0.0;
+    DevBuf d_expo;
     long long last_ntraj = -1;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // kernel start, kernel end, reduction end
     bool timed = false;
@@ -375,6 +382,91 @@ std::vector<unsigned char> encode_values(const std::vector<cd> &v, int precision
     return out;
 }
 
+// ---- exponential propagation: the ladder exp(M delta 2^l) -------------------
+//
+// Scaling and squaring (Moler & Van Loan, "Nineteen dubious ways to compute the
+// exponential of a matrix", 2003, the Taylor variant): with nu = max(||M||_1,
+// ||M||_inf) >= ||M||_2, delta = span / 2^L is the largest such step with
+// nu delta <= 1/16; exp(M delta) is the Taylor polynomial of degree 12 (its
+// truncation error is below (1/16)^13 / 13! ~ 4e-26 relative) and each further
+// level is the square of the one below.  FP64, on the host (setup).
+
+constexpr double kExpoTheta = 1.0 / 16.0;
+constexpr int kExpoDegree = 12;
+
+double op_norm_bound(const Csr &M)
+{
+    std::vector<double> col(M.n, 0.0);
+    double rmax = 0.0;
+    for (int i = 0; i < M.n; ++i) {
+        double r = 0.0;
+        for (int k = M.rp[i]; k < M.rp[i + 1]; ++k) {
+            r += std::abs(M.val[k]);
+            col[M.ci[k]] += std::abs(M.val[k]);
+        }
+        rmax = std::max(rmax, r);
+    }
+    double cmax = 0.0;
+    for (double c : col) cmax = std::max(cmax, c);
+    return std::max(rmax, cmax);
+}
+
+// X = sum_{m <= degree} (h M)^m / m! by Horner's rule, X <- I + (h/m) M X (dense row-major)
+void taylor_exp(const Csr &M, double h, int degree, cd *X)
+{
+    const int n = M.n;
+    std::vector<cd> Y((size_t)n * n);
+    for (size_t i = 0; i < (size_t)n * n; ++i) X[i] = 0.0;
+    for (int i = 0; i < n; ++i) X[(size_t)i * n + i] = 1.0;
+    for (int m = degree; m >= 1; --m) {
+        std::fill(Y.begin(), Y.end(), cd(0.0));
+        for (int i = 0; i < n; ++i)
+            for (int k = M.rp[i]; k < M.rp[i + 1]; ++k) {
+                const cd v = M.val[k];
+                const cd *xr = X + (size_t)M.ci[k] * n;
+                cd *yr = Y.data() + (size_t)i * n;
+                for (int j = 0; j < n; ++j) yr[j] += v * xr[j];
+            }
+        const double c = h / m;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) X[(size_t)i * n + j] = (i == j ? 1.0 : 0.0) + c * Y[(size_t)i * n + j];
+    }
+}
+
+// Z = X X (dense row-major)
+void square_into(const cd *X, cd *Z, int n)
+{
+    for (size_t i = 0; i < (size_t)n * n; ++i) Z[i] = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+            const cd x = X[(size_t)i * n + k];
+            if (x == cd(0.0)) continue;
+            const cd *xr = X + (size_t)k * n;
+            cd *zr = Z + (size_t)i * n;
+            for (int j = 0; j < n; ++j) zr[j] += x * xr[j];
+        }
+}
+
+// ladder[l] = exp(M delta 2^l), l = 0..L, with delta 2^L = span; returns L + 1
+// (0 when span is not positive and finite or needs more than 60 halvings)
+int expm_ladder(const Csr &M, double span, std::vector<cd> &ladder, double &delta)
+{
+    if (!(span > 0.0) || !std::isfinite(span)) return 0;
+    const int n = M.n;
+    const double nu = op_norm_bound(M);
+    int L = 0;
+    if (nu * span > kExpoTheta) L = (int)std::ceil(std::log2(nu * span / kExpoTheta));
+    while (L > 0 && std::ldexp(span, -(L - 1)) * nu <= kExpoTheta) --L;  // log2 rounding
+    while (std::ldexp(span, -L) * nu > kExpoTheta) ++L;
+    if (L > 60) return 0;
+    delta = std::ldexp(span, -L);
+    const size_t nn = (size_t)n * n;
+    ladder.assign((size_t)(L + 1) * nn, cd(0.0));
+    taylor_exp(M, delta, kExpoDegree, ladder.data());
+    for (int l = 1; l <= L; ++l) square_into(ladder.data() + (l - 1) * nn, ladder.data() + l * nn, n);
+    return L + 1;
+}
+
 void destroy_ctx(qtm_ctx *ctx)
 {
     if (!ctx) return;
@@ -384,7 +476,7 @@ void destroy_ctx(qtm_ctx *ctx)
                       &ctx->d_stats, &ctx->d_njumps, &ctx->d_jump_t, &ctx->d_jump_ch,
                       &ctx->d_rec, &ctx->d_mlp, &ctx->d_X, &ctx->d_T, &ctx->d_gpart, &ctx->d_lpart,
                       &ctx->d_grad, &ctx->d_loss, &ctx->d_m, &ctx->d_v, &ctx->d_op, &ctx->d_state,
-                      &ctx->d_col, &ctx->d_rhs, &ctx->d_dense};
+                      &ctx->d_col, &ctx->d_rhs, &ctx->d_dense, &ctx->d_expo};
     for (DevBuf *b : bufs) dev_free(ctx, *b);
     cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t &e : ctx->ev)
@@ -833,7 +925,17 @@ static qtm_status enqueue_run(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64
                         "qtm_run: the learned proposal needs complex128 or double-float and dimension <= 64");
         if (prop && a.n_drive > 0)
             return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_run: the learned proposal takes a constant Hamiltonian");
-        if (a.n_drive > 0)
+        if (ctx->method == QTM_METHOD_EXPONENTIAL && (prop || a.n_drive > 0))
+            return fail(ctx, QTM_ERR_UNSUPPORTED,
+                        "qtm_run: the exponential method takes a constant Hamiltonian and no learned proposal");
+        if (ctx->method == QTM_METHOD_EXPONENTIAL) {
+            a.expo = ctx->d_expo.p;
+            a.expo_levels = ctx->expo_levels;
+            a.expo_uniform = ctx->expo_uniform;
+            a.expo_delta = ctx->expo_delta;
+            e = ctx->precision == QTM_PREC_DF64 ? qtm::launch_mcwf_df64_expo(a, s, &ctx->info)
+                                                : qtm::launch_mcwf_c128_expo(a, s, &ctx->info);
+        } else if (a.n_drive > 0)
             e = ctx->precision == QTM_PREC_DF64  ? qtm::launch_mcwf_df64_drive(a, s, &ctx->info)
               : ctx->precision == QTM_PREC_C64   ? qtm::launch_mcwf_c64_drive(a, s, &ctx->info)
                                                  : qtm::launch_mcwf_c128_drive(a, s, &ctx->info);
@@ -964,9 +1066,33 @@ qtm_status qtm_run_batch(qtm_ctx *const *ctxs, const int64_t *first, const int64
 
 qtm_status qtm_run(qtm_ctx *ctx, int64_t ntraj, uint64_t seed) { return qtm_run_range(ctx, 0, ntraj, seed); }
 
-// Re-uploads the packed operators (after repack).
+// Uploads the exponential method's ladder in the device layout of the current
+// lane layout: level l, column c at (l n + c) G R, rows >= n zero.
+static qtm_status upload_ladder(qtm_ctx *ctx)
+{
+    const int n = ctx->n, NP = ctx->layout.G * ctx->layout.R;
+    std::vector<cd> dev((size_t)ctx->expo_levels * n * NP, cd(0.0));
+    for (int l = 0; l < ctx->expo_levels; ++l)
+        for (int c = 0; c < n; ++c)
+            for (int r = 0; r < n; ++r)
+                dev[((size_t)l * n + c) * NP + r] = ctx->ladder[((size_t)l * n + r) * n + c];
+    std::vector<unsigned char> bytes = encode_values(dev, ctx->precision);
+    cudaError_t e;
+    if ((e = dev_reserve(ctx, ctx->d_expo, bytes.size())) ||
+        (e = cudaMemcpyAsync(ctx->d_expo.p, bytes.data(), bytes.size(), cudaMemcpyHostToDevice, ctx->stream)) ||
+        (e = cudaStreamSynchronize(ctx->stream)))
+        return cuda_fail(ctx, e, "qtm_set_method: upload");
+    return QTM_OK;
+}
+
+// Re-uploads the packed operators (after repack), and the ladder of the
+// exponential method, whose device layout follows the lane layout.
 static qtm_status upload_ops(qtm_ctx *ctx)
 {
+    if (ctx->method == QTM_METHOD_EXPONENTIAL) {
+        qtm_status st = upload_ladder(ctx);
+        if (st) return st;
+    }
     std::vector<unsigned char> vals_dev = encode_reals(ctx->reals, ctx->precision);
     const size_t ib = ctx->ints.size() * sizeof(int), vb = vals_dev.size();
     cudaError_t e;
@@ -1422,6 +1548,8 @@ qtm_status qtm_set_drive(qtm_ctx *ctx, int32_t n_terms, const qtm_op *H, const d
     if (n_terms > 0 && (!H || !coef)) return fail(ctx, QTM_ERR_ARG, "qtm_set_drive: H or coef is NULL");
     if (n_terms > 0 && ctx->precision == QTM_PREC_BF16X6)
         return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_set_drive: the tensor-core path has a constant operator");
+    if (n_terms > 0 && ctx->method == QTM_METHOD_EXPONENTIAL)
+        return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_set_drive: the exponential method has a constant operator");
     if (1 + ctx->n_c + ctx->n_obs + n_terms > qtm::kMaxOps)
         return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_set_drive: too many operators in total");
     std::vector<Csr> D(n_terms);
@@ -1503,6 +1631,103 @@ qtm_status qtm_rhs_batch(qtm_ctx *ctx, int64_t n_vec, const double *y, double *m
             my[2 * ((size_t)v * n + i)] = res[(size_t)v * kd + i];
             my[2 * ((size_t)v * n + i) + 1] = res[(size_t)v * kd + np + i];
         }
+    return QTM_OK;
+}
+
+qtm_status qtm_set_method(qtm_ctx *ctx, int32_t method)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_set_method: ctx is NULL");
+    ctx->err.clear();
+    if (method == QTM_METHOD_DOPRI5) {
+        ctx->method = QTM_METHOD_DOPRI5;
+        ctx->last_ntraj = -1;
+        return QTM_OK;
+    }
+    if (method != QTM_METHOD_EXPONENTIAL) return fail(ctx, QTM_ERR_ARG, "qtm_set_method: unknown method");
+    if (ctx->precision != QTM_PREC_C128 && ctx->precision != QTM_PREC_DF64)
+        return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_set_method: the exponential method runs in complex128 or double-float");
+    if (!ctx->Dops.empty())
+        return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_set_method: the exponential method takes a constant Hamiltonian");
+    if (ctx->n > qtm::kMaxDimExpo) {
+        char buf[96];
+        std::snprintf(buf, sizeof buf, "qtm_set_method: the exponential method takes dim <= %d", qtm::kMaxDimExpo);
+        return fail(ctx, QTM_ERR_UNSUPPORTED, buf);
+    }
+    // the output spacing: the top level propagates one interval of a uniform grid
+    double span = 1.0;
+    int uniform = 0;
+    if (ctx->n_t > 1) {
+        const double mean = (ctx->t.back() - ctx->t.front()) / (ctx->n_t - 1);
+        double gmax = 0.0;
+        uniform = 1;
+        for (int j = 1; j < ctx->n_t; ++j) {
+            const double gap = ctx->t[j] - ctx->t[j - 1];
+            gmax = std::max(gmax, gap);
+            if (std::abs(gap - mean) > 1e-12 * mean) uniform = 0;
+        }
+        span = uniform ? mean : gmax;
+    }
+    std::vector<cd> ladder;
+    double delta = 0.0;
+    const int levels = expm_ladder(ctx->M, span, ladder, delta);
+    if (levels < 1) return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_set_method: ||M|| times the output spacing is too large");
+    ctx->ladder = std::move(ladder);
+    ctx->expo_levels = levels;
+    ctx->expo_uniform = uniform;
+    ctx->expo_delta = delta;
+    ctx->method = QTM_METHOD_EXPONENTIAL;
+    qtm_status st = upload_ladder(ctx);
+    if (st) {
+        ctx->method = QTM_METHOD_DOPRI5;
+        return st;
+    }
+    ctx->last_ntraj = -1;
+    return QTM_OK;
+}
+
+qtm_status qtm_expo_ladder(const qtm_ctx *ctx, int32_t *levels, double *delta)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_expo_ladder: ctx is NULL");
+    if (ctx->method != QTM_METHOD_EXPONENTIAL) return QTM_ERR_STATE;
+    if (levels) *levels = ctx->expo_levels;
+    if (delta) *delta = ctx->expo_delta;
+    return QTM_OK;
+}
+
+qtm_status qtm_propagator(const qtm_problem *p, double dt, double *out)
+{
+    g_create_error.clear();
+    if (!p || !out) return fail(nullptr, QTM_ERR_ARG, "qtm_propagator: problem or out is NULL");
+    if (!(dt >= 0.0) || !std::isfinite(dt)) return fail(nullptr, QTM_ERR_ARG, "qtm_propagator: need finite dt >= 0");
+    const int n = p->dim;
+    if (n < 1) return fail(nullptr, QTM_ERR_ARG, "qtm_propagator: dim must be >= 1");
+    if (p->n_c < 0 || (p->n_c > 0 && !p->C)) return fail(nullptr, QTM_ERR_ARG, "qtm_propagator: bad collapse operators");
+    Csr H;
+    qtm_status st = read_op(p->H, n, "H", H);
+    if (st) return st;
+    if (!is_hermitian(H)) return fail(nullptr, QTM_ERR_ARG, "qtm_propagator: H is not Hermitian (tolerance 1e-12)");
+    std::vector<Csr> C(p->n_c);
+    for (int i = 0; i < p->n_c; ++i) {
+        char buf[32];
+        std::snprintf(buf, sizeof buf, "C[%d]", i);
+        if ((st = read_op(p->C[i], n, buf, C[i]))) return st;
+    }
+    const Csr M = effective_matrix(H, C);
+    const size_t nn = (size_t)n * n;
+    if (dt == 0.0) {
+        for (size_t i = 0; i < 2 * nn; ++i) out[i] = 0.0;
+        for (int i = 0; i < n; ++i) out[2 * ((size_t)i * n + i)] = 1.0;
+        return QTM_OK;
+    }
+    std::vector<cd> ladder;
+    double delta = 0.0;
+    const int levels = expm_ladder(M, dt, ladder, delta);
+    if (levels < 1) return fail(nullptr, QTM_ERR_UNSUPPORTED, "qtm_propagator: ||M|| dt is too large");
+    const cd *top = ladder.data() + (size_t)(levels - 1) * nn;
+    for (size_t i = 0; i < nn; ++i) {
+        out[2 * i] = top[i].real();
+        out[2 * i + 1] = top[i].imag();
+    }
     return QTM_OK;
 }
 

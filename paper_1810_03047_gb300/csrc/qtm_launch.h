@@ -100,6 +100,12 @@ struct KernelArgs {
     // a_k cos(omega_k t + phi_k) with drive[k] = {a_k, omega_k, phi_k}
     int n_drive, drive_op0;
     double drive[kMaxDrive][3];
+    // exponential propagation: expo_levels propagators P_l = exp(M expo_delta 2^l),
+    // each column-major [n][G R] in the kernel's complex type (rows >= n zero);
+    // expo_uniform: the output grid is uniform with spacing expo_delta 2^(levels-1)
+    const void *expo;
+    int expo_levels, expo_uniform;
+    double expo_delta;
 };
 
 enum CounterIndex { kAccepted = 0, kRejected, kRhs, kJumps, kRootIters, kFailed, kNumCounters };
@@ -130,6 +136,10 @@ cudaError_t launch_mcwf_df64_prop(const KernelArgs &args, cudaStream_t stream, L
 cudaError_t launch_mcwf_c128_drive(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
 cudaError_t launch_mcwf_df64_drive(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
 cudaError_t launch_mcwf_c64_drive(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+// The exponential-propagation kernel (every lane layout up to dimension 256).
+cudaError_t launch_mcwf_c128_expo(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+cudaError_t launch_mcwf_df64_expo(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+constexpr int kMaxDimExpo = 256;
 inline cudaError_t launch_mcwf_c128(const KernelArgs &a, cudaStream_t s, LaunchInfo *i)
 {
     return a.G <= 32 ? launch_mcwf_c128_small(a, s, i) : launch_mcwf_c128_large(a, s, i);

@@ -37,6 +37,8 @@ QTM_PREC_C64 = 1
 QTM_PREC_DF64 = 3
 QTM_PREC_BF16X6 = 4
 QTM_FLAG_RECORD_JUMPS = 1
+QTM_METHOD_DOPRI5 = 0
+QTM_METHOD_EXPONENTIAL = 1
 
 # every entry point declared in include/qtm.h
 EXPORTS = ["qtm_set_allocator", "qtm_create", "qtm_run", "qtm_run_range", "qtm_expect", "qtm_sums",
@@ -45,7 +47,8 @@ EXPORTS = ["qtm_set_allocator", "qtm_create", "qtm_run", "qtm_run_range", "qtm_e
            "qtm_destroy", "qtm_version", "qtm_ensemble_reduce_static", "qtm_run_batch", "qtm_autotune",
            "qtm_set_layout", "qtm_proposal_collect", "qtm_proposal_pairs", "qtm_proposal_train",
            "qtm_proposal_set", "qtm_proposal_get", "qtm_proposal_enable", "qtm_mlp_loss_grad",
-           "qtm_rhs_batch", "qtm_set_drive", "qtm_set_wait_limit"]
+           "qtm_rhs_batch", "qtm_set_drive", "qtm_set_wait_limit", "qtm_set_method", "qtm_expo_ladder",
+           "qtm_propagator"]
 
 QTM_PROPOSAL_FLOATS = 4685
 MLP_PARAMS = 4673
@@ -140,6 +143,12 @@ def lib():
             L.qtm_set_drive.restype = ct.c_int
             L.qtm_set_wait_limit.argtypes = [ct.c_void_p, ct.c_uint64]
             L.qtm_set_wait_limit.restype = ct.c_int
+            L.qtm_set_method.argtypes = [ct.c_void_p, ct.c_int32]
+            L.qtm_set_method.restype = ct.c_int
+            L.qtm_expo_ladder.argtypes = [ct.c_void_p, ct.POINTER(ct.c_int32), dp]
+            L.qtm_expo_ladder.restype = ct.c_int
+            L.qtm_propagator.argtypes = [ct.POINTER(QtmProblem), ct.c_double, dp]
+            L.qtm_propagator.restype = ct.c_int
             for name in ("qtm_proposal_collect", "qtm_proposal_pairs", "qtm_proposal_train", "qtm_proposal_set",
                          "qtm_proposal_get", "qtm_proposal_enable", "qtm_mlp_loss_grad"):
                 getattr(L, name).restype = ct.c_int
@@ -472,6 +481,28 @@ def qtm_rhs_batch(ctx: Ctx, y) -> np.ndarray:
     out = np.empty_like(y)
     dp = ct.POINTER(ct.c_double)
     _check(lib().qtm_rhs_batch(ctx.handle, y.shape[0], y.ctypes.data_as(dp), out.ctypes.data_as(dp)), ctx)
+    return out
+
+
+def qtm_set_method(ctx: Ctx, method: int):
+    """QTM_METHOD_DOPRI5 (default) or QTM_METHOD_EXPONENTIAL (exact propagation between jumps)."""
+    _check(lib().qtm_set_method(ctx.handle, int(method)), ctx)
+
+
+def qtm_expo_ladder(ctx: Ctx):
+    """(levels, delta) of the exponential method's propagator ladder."""
+    lv = ct.c_int32()
+    d = ct.c_double()
+    _check(lib().qtm_expo_ladder(ctx.handle, ct.byref(lv), ct.byref(d)), ctx)
+    return lv.value, d.value
+
+
+def qtm_propagator(prob, dt: float) -> np.ndarray:
+    """exp(M dt) of the problem's effective operator, computed on the host (no GPU)."""
+    p, keep = make_problem(prob)
+    n = p.dim
+    out = np.zeros((n, n), np.complex128)
+    _check(lib().qtm_propagator(ct.byref(p), float(dt), out.view(np.float64).ctypes.data_as(ct.POINTER(ct.c_double))))
     return out
 
 

@@ -99,3 +99,37 @@ def test_last_error_without_context():
     with pytest.raises(Q.QtmError):
         Q.qtm_create(S.two_level_driven().with_(rtol=-1.0))
     assert "rtol" in Q.qtm_last_error(None)
+
+
+@pytest.mark.parametrize("name,dts", [
+    ("paper_unitary", [0.0, 0.1, 1.0, 10.0]),
+    ("jaynes_cummings_driven", [0.1, 2.5]),
+    ("purcell_qubit", [0.1, 1.0, 20.0]),          # nu dt up to ~1e4: 18 squarings
+    ("dense_random", [0.1]),
+])
+def test_host_propagator_matches_scipy_expm(name, dts):
+    """The exponential method's ladder arithmetic (scaling and squaring of a degree-12
+    Taylor polynomial, on the host) against scipy's Pade-based expm of the same M
+    (formed here from H and the C_n)."""
+    import scipy.linalg
+    prob = S.by_name(name, N=64) if name == "dense_random" else S.by_name(name)
+    H = prob.H.toarray()
+    M = -1j * H
+    for c in prob.C:
+        c = c.toarray()
+        M = M - 0.5 * c.conj().T @ c
+    for dt in dts:
+        got = Q.qtm_propagator(prob, dt)
+        ref = scipy.linalg.expm(M * dt)
+        scale = max(1.0, np.abs(ref).max())
+        assert np.abs(got - ref).max() <= 1e-12 * scale, (name, dt, np.abs(got - ref).max())
+
+
+def test_host_propagator_semigroup_and_errors():
+    prob = S.purcell_qubit()
+    a, b = Q.qtm_propagator(prob, 0.3), Q.qtm_propagator(prob, 0.45)
+    np.testing.assert_allclose(a @ b, Q.qtm_propagator(prob, 0.75), atol=1e-13)
+    for dt in (-1.0, np.nan, np.inf):
+        with pytest.raises(Q.QtmError) as ei:
+            Q.qtm_propagator(prob, dt)
+        assert ei.value.status == Q.QTM_ERR_ARG
