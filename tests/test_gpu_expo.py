@@ -19,8 +19,14 @@ from test_gpu_parity import PRECS, _within_statistics, gpu_run
 pytestmark = pytest.mark.gpu
 
 MAXJ = 64
+# Both sides' propagators carry rounding: the ladder (scaling and squaring, up to
+# 2^L amplification of the Taylor polynomial's rounding) and scipy's expm (Pade
+# with its own squarings) differ by up to ~6e-14 per output interval on the
+# stiff system (3e-14 each from a third route).  Over the m intervals between
+# two jumps the squared norm thus moves by ~m 1e-13, which shifts a crossing by
+# that over the decay rate (~0.5 r): 1e-11 .. 1e-10 after tens of intervals.
 TOL_TAU = 1e-9                # every jump time, relative to max(1, tau)
-TOL_TAU_MEDIAN = {Q.QTM_PREC_C128: 1e-12, Q.QTM_PREC_DF64: 1e-10}
+TOL_TAU_MEDIAN = {Q.QTM_PREC_C128: 1e-10, Q.QTM_PREC_DF64: 5e-10}
 TOL_OBS = 1e-8                # every per-trajectory observable
 TOL_ENSEMBLE = 1e-10
 
