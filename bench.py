@@ -711,6 +711,16 @@ def exponential_method(Q, torch, stream, world, rank, dist, pk, jc_ref_mean, ntr
         "observable_error_expo_c128_vs_dopri5_c128": float(np.abs(r["expo_c128"]["mean"] - ref).max()),
         "observable_error_expo_df64_vs_dopri5_c128": float(np.abs(r["expo_df64"]["mean"] - ref).max()),
     }
+    if world == 1 and rank == 0:
+        # the exact-propagation oracle (scipy expm + brentq, one host core) on a bounded sample
+        from oracle import exact
+        t0 = time.perf_counter()
+        sample = exact.mcwf(stiff, ntraj=200)
+        dt = time.perf_counter() - t0
+        out["stiff_purcell"]["oracle_cpu"] = {"value": 200 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                              "sample": "trajectory ids 0..199 of the same workload "
+                                                        "(oracle/exact.py, single thread)"}
+        del sample
     prob, _, _ = workload(ntraj)
     j = {}
     for key, prec in (("expo_df64", Q.QTM_PREC_DF64), ("expo_c128", Q.QTM_PREC_C128)):
@@ -731,6 +741,42 @@ def exponential_method(Q, torch, stream, world, rank, dist, pk, jc_ref_mean, ntr
                                "flops_note": "8 N^2 per trajectory and output interval (P_L x); the "
                                              "observables, jumps and Taylor products are not counted"}
     out["jaynes_cummings"] = jc
+    # dense operators: one dense product per output interval instead of six per
+    # Dormand-Prince step; against the complex128 Dormand-Prince path on the first
+    # 2,000 ids and the tensor-core engine's figure (reported in its own leg)
+    dense = S.dense_random(ntraj=ntraj)
+    dres = {}
+    for key, prec in (("expo_df64", Q.QTM_PREC_DF64), ("expo_c128", Q.QTM_PREC_C128)):
+        dres[key] = _timed_passes(Q, torch, stream, world, dist, dense, prec, E, first, count, passes=1)
+        launches += dres[key].pop("launches")
+    sample = min(count, 2000)
+    ctx = Q.qtm_create(dense, stream=int(stream.cuda_stream), precision=Q.QTM_PREC_C128)
+    Q.qtm_run_range(ctx, first, sample, dense.seed)
+    ref_traj = Q.qtm_traj_expect(ctx)
+    ref_ms = Q.qtm_stats(ctx)["kernel_ms"]
+    Q.qtm_destroy(ctx)
+    launches += 5
+    ctx = Q.qtm_create(dense, stream=int(stream.cuda_stream), precision=Q.QTM_PREC_DF64)
+    Q.qtm_set_method(ctx, E)
+    Q.qtm_run_range(ctx, first, sample, dense.seed)
+    ex_traj = Q.qtm_traj_expect(ctx)
+    Q.qtm_destroy(ctx)
+    launches += 5
+    nd = dense.dim
+    dj = {"workload": "dense random open system (GUE H, N=256, 4 Ginibre C_n), 101 outputs on [0, 10], "
+                      f"{world * count} trajectories", "unit": UNIT,
+          "dopri5_c128_sample": {"value": sample / (ref_ms / 1e3), "kernel_ms": ref_ms, "sample": sample},
+          "observable_error_expo_df64_vs_dopri5_c128": float(np.abs(ex_traj.mean(axis=0)
+                                                                    - ref_traj.mean(axis=0)).max()),
+          "observable_error_note": f"max |mean - complex128 Dormand-Prince mean| over the first {sample} ids"}
+    for key, peak_key in (("expo_df64", "df64"), ("expo_c128", "c128")):
+        v = dres[key]
+        achieved = 8.0 * nd * nd * (len(dense.t) - 1) * count / (v["kernel_ms"] / 1e3) / 1e12
+        peak, note = pk[peak_key]
+        dj[key] = {kk: vv for kk, vv in v.items() if kk != "mean"}
+        dj[key]["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                               "frac": achieved / peak, "traffic": None, "peak_note": note}
+    out["dense_random"] = dj
     out["launches"] = launches
     return out
 

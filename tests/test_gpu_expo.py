@@ -78,6 +78,9 @@ CASES = [
     ("jaynes_cummings_driven", dict(), 24),              # N = 60, many jumps
     ("dense_random", dict(N=64, ntraj=16), 16),          # dense: the 64-lane layout
     ("ising_L7", dict(ntraj=6), 6),                      # N = 128: two warps per trajectory
+    ("fock_decay", dict(n0=3, kappa=0.5), 100),          # closed-form jump times, forced channel
+    ("paper_jaynes_cummings", dict(), 1),                # Sec. 4.3: closed system (no channel), N = 80
+    ("dense_random", dict(N=256, ntraj=4), 4),           # the dense workload's size: four warps per trajectory
 ]
 
 
@@ -186,3 +189,21 @@ def test_expo_argument_errors():
         Q.qtm_set_method(big, Q.QTM_METHOD_EXPONENTIAL)
     assert ei.value.status == Q.QTM_ERR_UNSUPPORTED
     Q.qtm_destroy(big)
+
+
+def test_expo_in_a_batch_with_a_dopri5_context():
+    """qtm_run_batch runs an exponential-method context beside a Dormand-Prince one
+    in one CUDA graph; each gives its single-run result bitwise."""
+    stiff = S.purcell_qubit()
+    jc = S.jaynes_cummings_driven()
+    a = Q.qtm_create(stiff)
+    Q.qtm_set_method(a, Q.QTM_METHOD_EXPONENTIAL)
+    b = Q.qtm_create(jc)
+    Q.qtm_run_batch([a, b], [300, 100], seed=1)
+    got_a, got_b = Q.qtm_traj_expect(a), Q.qtm_traj_expect(b)
+    Q.qtm_run(a, 300, 1)
+    Q.qtm_run(b, 100, 1)
+    np.testing.assert_array_equal(got_a, Q.qtm_traj_expect(a))
+    np.testing.assert_array_equal(got_b, Q.qtm_traj_expect(b))
+    Q.qtm_destroy(a)
+    Q.qtm_destroy(b)
