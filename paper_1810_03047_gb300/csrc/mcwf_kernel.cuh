@@ -598,16 +598,40 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
 #pragma unroll 1
         for (int s = 1; s < 7; ++s) {
             b = L.xnext();
+            if constexpr (Ar::kRowChains) {
+                // the lane's R rows advance together: R independent accumulation chains
+                typename Ar::acc acc[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) acc[r] = Ar::zero();
 #pragma unroll 1
-            for (int r = 0; r < R; ++r) {
-                const int row = gl + G * r;
-                if (row < n) {
-                    typename Ar::acc acc = Ar::zero();
+                for (int q = 0; q < s; ++q) {
+                    const typename Ar::coef c = C.a[s][q];
+                    const cplx *kq = L.kq(q);
+#pragma unroll
+                    for (int r = 0; r < R; ++r)
+                        if (gl + G * r < n) Ar::axpy(acc[r], c, kq[gl + G * r]);
+                }
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int row = gl + G * r;
+                    if (row < n) {
+                        const cplx y = Ar::add_scaled(psi[row], hc, acc[r]);
+                        b[row] = y;
+                        if (s == 6) yn[row] = y;
+                    }
+                }
+            } else {
 #pragma unroll 1
-                    for (int q = 0; q < s; ++q) Ar::axpy(acc, C.a[s][q], L.kq(q)[row]);
-                    const cplx y = Ar::add_scaled(psi[row], hc, acc);
-                    b[row] = y;
-                    if (s == 6) yn[row] = y;
+                for (int r = 0; r < R; ++r) {
+                    const int row = gl + G * r;
+                    if (row < n) {
+                        typename Ar::acc acc = Ar::zero();
+#pragma unroll 1
+                        for (int q = 0; q < s; ++q) Ar::axpy(acc, C.a[s][q], L.kq(q)[row]);
+                        const cplx y = Ar::add_scaled(psi[row], hc, acc);
+                        b[row] = y;
+                        if (s == 6) yn[row] = y;
+                    }
                 }
             }
             g.sync();
@@ -619,16 +643,39 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
 
         typename Ar::errt esum = 0;
         typename Ar::red nr = Ar::rzero();
+        if constexpr (!Ar::kRowChains) {
 #pragma unroll 1
-        for (int r = 0; r < R; ++r) {
-            const int row = gl + G * r;
-            if (row < n) {
-                typename Ar::acc e = Ar::zero();
+            for (int r = 0; r < R; ++r) {
+                const int row = gl + G * r;
+                if (row < n) {
+                    typename Ar::acc e = Ar::zero();
 #pragma unroll 1
-                for (int q = 0; q < 7; ++q)
-                    if (q != 1) Ar::axpy(e, C.e[q], L.kq(q)[row]);
-                esum += Ar::err_term(e, h, psi[row], yn[row], rtol, atol);
-                nr = Ar::radd(nr, Ar::abs2(yn[row]));
+                    for (int q = 0; q < 7; ++q)
+                        if (q != 1) Ar::axpy(e, C.e[q], L.kq(q)[row]);
+                    esum += Ar::err_term(e, h, psi[row], yn[row], rtol, atol);
+                    nr = Ar::radd(nr, Ar::abs2(yn[row]));
+                }
+            }
+        } else {
+            typename Ar::acc e[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) e[r] = Ar::zero();
+#pragma unroll 1
+            for (int q = 0; q < 7; ++q) {
+                if (q == 1) continue;
+                const typename Ar::coef c = C.e[q];
+                const cplx *kq = L.kq(q);
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    if (gl + G * r < n) Ar::axpy(e[r], c, kq[gl + G * r]);
+            }
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int row = gl + G * r;
+                if (row < n) {
+                    esum += Ar::err_term(e[r], h, psi[row], yn[row], rtol, atol);
+                    nr = Ar::radd(nr, Ar::abs2(yn[row]));
+                }
             }
         }
         const double err = Ar::err_final(Ar::err_sum(g, esum), n);

@@ -161,6 +161,9 @@ __device__ __forceinline__ df group_sum_df(const Group<G> &g, df v)
 
 struct ArF64 {
     static constexpr int kId = 0;
+    // Stage and error sums advance the lane's rows together (independent
+    // accumulation chains); measured faster than row by row for this arithmetic.
+    static constexpr bool kRowChains = true;
     using cplx = cpx<double>;
     using real = double;
     using coef = double;
@@ -252,6 +255,9 @@ struct __align__(16) cdf {
 
 struct ArDF {
     static constexpr int kId = 1;
+    // Stage sums row by row (rolled): interleaving the lane's rows into
+    // independent chains measured 7 % slower for this arithmetic.
+    static constexpr bool kRowChains = false;
     using cplx = cdf;
     using real = df;
     using coef = df;
@@ -360,6 +366,9 @@ struct ArDF {
 
 struct ArF32 {
     static constexpr int kId = 2;
+    // Stage and error sums advance the lane's rows together (independent
+    // accumulation chains); measured faster than row by row for this arithmetic.
+    static constexpr bool kRowChains = true;
     using cplx = cpx<float>;
     using real = float;
     using coef = float;
