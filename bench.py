@@ -42,6 +42,17 @@ if ROOT not in sys.path:
 METRIC = "trajectories/sec at ≤1e-5 observable error vs plain FP64 GPU path; roofline %"
 UNIT = "trajectories/s"
 
+# DRAM bytes (read + write) of one launch at full size, from one ncu capture with
+# `--metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+# --clock-control none -s 1 -c 1` (one pass) of the timed launch of
+# `python bench.py --only df64 --steps 1 --warmup 1` (-k regex:mcwf_kernel) and
+# `python bench.py --only dense --steps 1 --warmup 1` (-k regex:dense_tc_kernel).
+# Valid for the kernels as captured; a change to a kernel voids its entry.
+TRAFFIC_PER_LAUNCH = {
+    "qtm::mcwf_kernel<df64,32,2>": 4.82e6 + 101.55e6,    # 20,000 JC trajectories: the outputs
+    "qtm::dense_tc_kernel<256>": 184.81e9 + 51.10e9,     # 20,000 dense trajectories: the state block
+}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -328,7 +339,10 @@ def main():
                 "kernel_ms": kern, "mean": mean, "stats": last, "launches": launches,
                 "attempts_per_traj": attempts / steps / ntraj,
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                             "frac": achieved / peak, "traffic": None,
+                             "frac": achieved / peak,
+                             "traffic": TRAFFIC_PER_LAUNCH.get(
+                                 f"qtm::mcwf_kernel<{prec_name},{last['kernel_group']},{last['kernel_rows']}>")
+                             if ntraj == 20000 else None,
                              "kernel": f"qtm::mcwf_kernel<{prec_name},{last['kernel_group']},{last['kernel_rows']}>",
                              "peak_note": note, "kernel_ms": kern}}
 
@@ -642,7 +656,9 @@ def dense_tensor_core(Q, torch, stream, world, rank, dist, pk, ntraj=20000, samp
             "observable_error_note": f"max |mean - complex128 mean| over the first {sample} trajectory ids",
             "steps_per_trajectory": attempts / 2 / count,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "qtm::dense_tc_kernel<256>",
+                         "frac": achieved / peak,
+                         "traffic": TRAFFIC_PER_LAUNCH["qtm::dense_tc_kernel<256>"] if count == 20000 else None,
+                         "kernel": "qtm::dense_tc_kernel<256>",
                          "bytes_per_attempt": bytes_per_attempt, "peak_note": note, "kernel_ms": kms},
             "launches": 3 * 5 + 5}
 
