@@ -713,6 +713,7 @@ def exponential_method(Q, torch, stream, world, rank, dist, pk, jc_ref_mean, ntr
     stiff = S.purcell_qubit(ntraj=ntraj)
     r = {}
     for key, prec, meth in (("expo_df64", Q.QTM_PREC_DF64, E), ("expo_c128", Q.QTM_PREC_C128, E),
+                            ("expo_c64", Q.QTM_PREC_C64, E),
                             ("dopri5_df64", Q.QTM_PREC_DF64, D), ("dopri5_c128", Q.QTM_PREC_C128, D)):
         r[key] = _timed_passes(Q, torch, stream, world, dist, stiff, prec, meth, first, count)
         launches += r[key].pop("launches")
@@ -726,6 +727,7 @@ def exponential_method(Q, torch, stream, world, rank, dist, pk, jc_ref_mean, ntr
         "speedup_expo_c128_vs_dopri5_c128": r["expo_c128"]["value"] / r["dopri5_c128"]["value"],
         "observable_error_expo_c128_vs_dopri5_c128": float(np.abs(r["expo_c128"]["mean"] - ref).max()),
         "observable_error_expo_df64_vs_dopri5_c128": float(np.abs(r["expo_df64"]["mean"] - ref).max()),
+        "observable_error_expo_c64_vs_dopri5_c128": float(np.abs(r["expo_c64"]["mean"] - ref).max()),
     }
     if world == 1 and rank == 0:
         # the exact-propagation oracle (scipy expm + brentq, one host core) on a bounded sample
@@ -739,14 +741,14 @@ def exponential_method(Q, torch, stream, world, rank, dist, pk, jc_ref_mean, ntr
         del sample
     prob, _, _ = workload(ntraj)
     j = {}
-    for key, prec in (("expo_df64", Q.QTM_PREC_DF64), ("expo_c128", Q.QTM_PREC_C128)):
+    for key, prec in (("expo_df64", Q.QTM_PREC_DF64), ("expo_c128", Q.QTM_PREC_C128), ("expo_c64", Q.QTM_PREC_C64)):
         j[key] = _timed_passes(Q, torch, stream, world, dist, prob, prec, E, first, count)
         launches += j[key].pop("launches")
     n = prob.dim
     flops = 8.0 * n * n * (len(prob.t) - 1)  # the output-interval products, per trajectory
     jc = {"workload": f"damped driven Jaynes-Cummings (N=60), 401 outputs on [0, 40], {world * count} trajectories",
           "unit": UNIT}
-    for key, peak_key in (("expo_df64", "df64"), ("expo_c128", "c128")):
+    for key, peak_key in (("expo_df64", "df64"), ("expo_c128", "c128"), ("expo_c64", "c64")):
         v = j[key]
         achieved = flops * count / (v["kernel_ms"] / 1e3) / 1e12
         peak, note = pk[peak_key]
@@ -762,7 +764,7 @@ def exponential_method(Q, torch, stream, world, rank, dist, pk, jc_ref_mean, ntr
     # 2,000 ids and the tensor-core engine's figure (reported in its own leg)
     dense = S.dense_random(ntraj=ntraj)
     dres = {}
-    for key, prec in (("expo_df64", Q.QTM_PREC_DF64), ("expo_c128", Q.QTM_PREC_C128)):
+    for key, prec in (("expo_df64", Q.QTM_PREC_DF64), ("expo_c128", Q.QTM_PREC_C128), ("expo_c64", Q.QTM_PREC_C64)):
         dres[key] = _timed_passes(Q, torch, stream, world, dist, dense, prec, E, first, count, passes=1)
         launches += dres[key].pop("launches")
     sample = min(count, 2000)
@@ -772,20 +774,24 @@ def exponential_method(Q, torch, stream, world, rank, dist, pk, jc_ref_mean, ntr
     ref_ms = Q.qtm_stats(ctx)["kernel_ms"]
     Q.qtm_destroy(ctx)
     launches += 5
-    ctx = Q.qtm_create(dense, stream=int(stream.cuda_stream), precision=Q.QTM_PREC_DF64)
-    Q.qtm_set_method(ctx, E)
-    Q.qtm_run_range(ctx, first, sample, dense.seed)
-    ex_traj = Q.qtm_traj_expect(ctx)
-    Q.qtm_destroy(ctx)
-    launches += 5
+    ex_traj = {}
+    for key, prec in (("expo_df64", Q.QTM_PREC_DF64), ("expo_c64", Q.QTM_PREC_C64)):
+        ctx = Q.qtm_create(dense, stream=int(stream.cuda_stream), precision=prec)
+        Q.qtm_set_method(ctx, E)
+        Q.qtm_run_range(ctx, first, sample, dense.seed)
+        ex_traj[key] = Q.qtm_traj_expect(ctx)
+        Q.qtm_destroy(ctx)
+        launches += 5
     nd = dense.dim
     dj = {"workload": "dense random open system (GUE H, N=256, 4 Ginibre C_n), 101 outputs on [0, 10], "
                       f"{world * count} trajectories", "unit": UNIT,
           "dopri5_c128_sample": {"value": sample / (ref_ms / 1e3), "kernel_ms": ref_ms, "sample": sample},
-          "observable_error_expo_df64_vs_dopri5_c128": float(np.abs(ex_traj.mean(axis=0)
+          "observable_error_expo_df64_vs_dopri5_c128": float(np.abs(ex_traj["expo_df64"].mean(axis=0)
                                                                     - ref_traj.mean(axis=0)).max()),
+          "observable_error_expo_c64_vs_dopri5_c128": float(np.abs(ex_traj["expo_c64"].mean(axis=0)
+                                                                   - ref_traj.mean(axis=0)).max()),
           "observable_error_note": f"max |mean - complex128 Dormand-Prince mean| over the first {sample} ids"}
-    for key, peak_key in (("expo_df64", "df64"), ("expo_c128", "c128")):
+    for key, peak_key in (("expo_df64", "df64"), ("expo_c128", "c128"), ("expo_c64", "c64")):
         v = dres[key]
         achieved = 8.0 * nd * nd * (len(dense.t) - 1) * count / (v["kernel_ms"] / 1e3) / 1e12
         peak, note = pk[peak_key]

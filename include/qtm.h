@@ -402,9 +402,11 @@ qtm_status qtm_rhs_batch(qtm_ctx *ctx, int64_t n_vec, const double *y, double *m
 
 /* Selects the method of later runs.  QTM_METHOD_EXPONENTIAL computes and uploads
  * the ladder (host FP64, O(L n^3 + 12 nnz(M) n) operations; (L + 1) n^2 complex
- * values of device memory) and needs QTM_PREC_C128 or QTM_PREC_DF64, dimension
- * <= 256 and no time-dependent terms (QTM_ERR_UNSUPPORTED otherwise; the learned
- * proposal is refused by qtm_run).  QTM_METHOD_DOPRI5 restores the default.
+ * values of device memory, rounded to the context's arithmetic) and needs
+ * QTM_PREC_C128, QTM_PREC_DF64 or QTM_PREC_C64 (FP32 propagators and state,
+ * double-float norms: a trajectory's jump times move by about the FP32 rounding
+ * accumulated over the products), dimension <= 256 and no time-dependent terms
+ * (QTM_ERR_UNSUPPORTED otherwise; the learned proposal is refused by qtm_run).  QTM_METHOD_DOPRI5 restores the default.
  * QTM_ERR_ARG for any other value. */
 qtm_status qtm_set_method(qtm_ctx *ctx, int32_t method);
 

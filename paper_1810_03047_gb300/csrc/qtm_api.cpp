@@ -933,8 +933,9 @@ static qtm_status enqueue_run(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64
             a.expo_levels = ctx->expo_levels;
             a.expo_uniform = ctx->expo_uniform;
             a.expo_delta = ctx->expo_delta;
-            e = ctx->precision == QTM_PREC_DF64 ? qtm::launch_mcwf_df64_expo(a, s, &ctx->info)
-                                                : qtm::launch_mcwf_c128_expo(a, s, &ctx->info);
+            e = ctx->precision == QTM_PREC_DF64  ? qtm::launch_mcwf_df64_expo(a, s, &ctx->info)
+              : ctx->precision == QTM_PREC_C64   ? qtm::launch_mcwf_c64_expo(a, s, &ctx->info)
+                                                 : qtm::launch_mcwf_c128_expo(a, s, &ctx->info);
         } else if (a.n_drive > 0)
             e = ctx->precision == QTM_PREC_DF64  ? qtm::launch_mcwf_df64_drive(a, s, &ctx->info)
               : ctx->precision == QTM_PREC_C64   ? qtm::launch_mcwf_c64_drive(a, s, &ctx->info)
@@ -1644,8 +1645,8 @@ qtm_status qtm_set_method(qtm_ctx *ctx, int32_t method)
         return QTM_OK;
     }
     if (method != QTM_METHOD_EXPONENTIAL) return fail(ctx, QTM_ERR_ARG, "qtm_set_method: unknown method");
-    if (ctx->precision != QTM_PREC_C128 && ctx->precision != QTM_PREC_DF64)
-        return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_set_method: the exponential method runs in complex128 or double-float");
+    if (ctx->precision == QTM_PREC_BF16X6)
+        return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_set_method: the tensor-core engine integrates with Dormand-Prince");
     if (!ctx->Dops.empty())
         return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_set_method: the exponential method takes a constant Hamiltonian");
     if (ctx->n > qtm::kMaxDimExpo) {

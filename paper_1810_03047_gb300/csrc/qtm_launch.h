@@ -139,6 +139,7 @@ cudaError_t launch_mcwf_c64_drive(const KernelArgs &args, cudaStream_t stream, L
 // The exponential-propagation kernel (every lane layout up to dimension 256).
 cudaError_t launch_mcwf_c128_expo(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
 cudaError_t launch_mcwf_df64_expo(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+cudaError_t launch_mcwf_c64_expo(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
 constexpr int kMaxDimExpo = 256;
 inline cudaError_t launch_mcwf_c128(const KernelArgs &a, cudaStream_t s, LaunchInfo *i)
 {

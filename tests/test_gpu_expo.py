@@ -160,12 +160,11 @@ def test_expo_switch_back_to_dopri5_is_bitwise_the_default():
 
 def test_expo_argument_errors():
     prob = S.purcell_qubit(ntraj=4)
-    for prec in (Q.QTM_PREC_C64, Q.QTM_PREC_BF16X6):
-        ctx = Q.qtm_create(prob, precision=prec)
-        with pytest.raises(Q.QtmError) as ei:
-            Q.qtm_set_method(ctx, Q.QTM_METHOD_EXPONENTIAL)
-        assert ei.value.status == Q.QTM_ERR_UNSUPPORTED
-        Q.qtm_destroy(ctx)
+    ctx = Q.qtm_create(prob, precision=Q.QTM_PREC_BF16X6)
+    with pytest.raises(Q.QtmError) as ei:
+        Q.qtm_set_method(ctx, Q.QTM_METHOD_EXPONENTIAL)
+    assert ei.value.status == Q.QTM_ERR_UNSUPPORTED
+    Q.qtm_destroy(ctx)
     ctx = Q.qtm_create(prob)
     with pytest.raises(Q.QtmError) as ei:
         Q.qtm_set_method(ctx, 7)
@@ -207,3 +206,26 @@ def test_expo_in_a_batch_with_a_dopri5_context():
     np.testing.assert_array_equal(got_b, Q.qtm_traj_expect(b))
     Q.qtm_destroy(a)
     Q.qtm_destroy(b)
+
+
+@pytest.mark.parametrize("name,kw,ntraj", [("purcell_qubit", dict(), 400), ("jaynes_cummings_driven", dict(), 200),
+                                           ("dense_random", dict(N=64, ntraj=100), 100)])
+def test_expo_complex64_statistics(orc, name, kw, ntraj):
+    """complex64 (FP32 propagators and state, double-float norms): the same jump
+    count as the exact oracle for the bulk of the trajectories, jump times within
+    the FP32 rounding over the decay rate, and the ensemble within its statistics
+    of the Lindblad solution."""
+    prob = S.by_name(name, **kw)
+    g = expo_run(prob, ntraj, precision=Q.QTM_PREC_C64)
+    o = exact_run(prob, ntraj)
+    same = g["n_jumps"] == o["n_jumps"]
+    assert same.mean() >= 0.95
+    dts = []
+    for i in np.where(same)[0]:
+        k = min(int(o["n_jumps"][i]), MAXJ)
+        dts.append(np.abs(g["jump_t"][i, :k] - o["jump_t"][i, :k]))
+    dts = np.concatenate(dts)
+    assert np.median(dts) <= 1e-4, np.median(dts)
+    assert g["stats"]["failed"] == 0
+    L, _ = orc.lindblad(prob, 1e-10, 1e-12)
+    _within_statistics(g["mean"], g["se"], L, ntraj)
