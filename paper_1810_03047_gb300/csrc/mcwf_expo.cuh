@@ -6,10 +6,12 @@
 //
 // The host precomputes a ladder of propagators P_l = exp(M delta 2^l),
 // l = 0..L, with delta chosen so that nu delta <= 1/16 (nu >= ||M||_2) and
-// delta 2^L = the output spacing.  Per trajectory (G lanes, R rows per lane,
-// vectors in shared memory as in mcwf_kernel.cuh):
-//   * between outputs: psi(t_j) = P_L psi(t_{j-1}) on a uniform grid (one dense
-//     product); otherwise the duration d is split into its binary digits in
+// delta 2^L = the output spacing.  A group of G lanes (R rows per lane, vectors
+// in shared memory as in mcwf_kernel.cuh) carries T trajectories in lock step
+// from output to output:
+//   * between outputs: psi_t(t_j) = P_L psi_t(t_{j-1}) for all T trajectories in
+//     one pass over P_L on a uniform grid (each column of P_L loaded once for T
+//     products); otherwise, per trajectory, the duration d is split into its binary digits in
 //     units of delta (one product per digit) and a remainder s < delta, which
 //     takes a degree-9 Taylor polynomial of exp(s M) (9 products with M; the
 //     truncation error is below 3e-19 relative);
@@ -21,7 +23,9 @@
 //     (u_m = M^m psi / m!) is solved for r by Newton's method with a bisection
 //     safeguard;
 //   * (C), (D) as in the Dormand-Prince kernel (apply_jump, new draws), and the
-//     propagation restarts at tau.
+//     propagation restarts at tau and continues to t_j; a trajectory's crossings
+//     are handled one trajectory at a time with the group's shared scratch
+//     vectors, so after each output step every trajectory of the group is at t_j.
 // No step-size control and no interpolation are involved: a trajectory differs
 // from the exact one by rounding and by the root tolerance only, whatever the
 // stiffness of M.
@@ -33,44 +37,61 @@ namespace qtm {
 
 constexpr int kExpoTaylor = 9;  // degree of the Taylor polynomial of exp(s M), s <= delta
 
-// Vector slots of one trajectory group: the state, two product buffers and the
-// Taylor vectors u_1..u_9.  u_1 sits in the slot apply_jump uses as scratch (it
-// is dead once the jump time is known).
-enum ExpoSlot { kEPsi = 0, kEA = 1, kEU = 2, kEB = kEU + kExpoTaylor, kNumExpoSlots = kEB + 1 };
-static_assert(kEU == kYn && kEPsi == kPsi, "apply_jump writes slot kPsi and uses slot kYn as scratch");
+// Vector slots of a group of T trajectories: psi_t and the batched product y_t
+// per trajectory, then the shared scratch (two product buffers and the Taylor
+// vectors u_1..u_9, used by one trajectory at a time; u_1 doubles as the jump's
+// scratch, since it is dead once the jump time is known).
+template <int T>
+struct ExpoSlots {
+    static constexpr int kPsi = 0, kY = T, kA = 2 * T, kB = 2 * T + 1, kU = 2 * T + 2;
+    static constexpr int kCount = kU + kExpoTaylor;
+};
 
-// out = P x on the lane's rows; P is column-major with G R rows per column (zero
-// below n).  Returns the lane's part of ||out||^2.  x is synchronised.
-template <class Ar, int G, int R>
-__device__ __forceinline__ typename Ar::red level_apply(const typename Ar::cplx *__restrict__ P,
-                                                        const typename Ar::cplx *x, typename Ar::cplx *out,
-                                                        int gl, int n)
+// out_t = P x_t for t < T (x_t = x + t NP, out_t = out + t NP) on the lane's rows;
+// P is column-major with NP = G R rows per column (zero below n), so every
+// column is loaded once for the T products.  nn[t] = the lane's part of
+// ||out_t||^2.  The x_t are synchronised.
+template <class Ar, int G, int R, int T>
+__device__ __forceinline__ void level_apply(const typename Ar::cplx *__restrict__ P, const typename Ar::cplx *x,
+                                            typename Ar::cplx *out, int gl, int n, typename Ar::red (&nn)[T])
 {
     constexpr int NP = G * R;
-    typename Ar::acc acc[R];
+    typename Ar::acc acc[T][R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = Ar::zero();
+    for (int t = 0; t < T; ++t)
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[t][r] = Ar::zero();
     const typename Ar::cplx *col = P + gl;
-#pragma unroll 4
+#pragma unroll 2
     for (int c = 0; c < n; ++c) {
-        const typename Ar::cplx xc = x[c];
+        typename Ar::cplx p[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) Ar::mac(acc[r], col[G * r], xc);
+        for (int r = 0; r < R; ++r) p[r] = col[G * r];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const typename Ar::cplx xc = x[t * NP + c];
+#pragma unroll
+            for (int r = 0; r < R; ++r) Ar::mac(acc[t][r], p[r], xc);
+        }
         col += NP;
     }
-    typename Ar::red nn = Ar::rzero();
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int row = gl + G * r;
-        if (row < n) {
-            const typename Ar::cplx v = Ar::get(acc[r]);
-            out[row] = v;
-            nn = Ar::radd(nn, Ar::abs2(v));
+    for (int t = 0; t < T; ++t) {
+        nn[t] = Ar::rzero();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int row = gl + G * r;
+            if (row < n) {
+                const typename Ar::cplx v = Ar::get(acc[t][r]);
+                out[t * NP + row] = v;
+                nn[t] = Ar::radd(nn[t], Ar::abs2(v));
+            }
         }
     }
-    return nn;
 }
 
+// One trajectory's propagation and crossing search with the group's shared
+// scratch vectors A, B and U (u_m at U + (m - 1) NP).
 template <class Ar, int G, int R>
 struct Expo {
     using cplx = typename Ar::cplx;
@@ -78,17 +99,17 @@ struct Expo {
     const KernelArgs &a;
     const Group<G> &g;
     CsrView<Ar> M;
-    cplx *v;  // the group's slots
+    cplx *A, *B, *U;
     unsigned long long n_rhs = 0, n_rej = 0;
     int root_iters = 0;
 
-    __device__ cplx *slot(int s) const { return v + s * NP; }
     __device__ const cplx *level(int l) const
     {
         return static_cast<const cplx *>(a.expo) + (size_t)l * a.n * NP;
     }
+    __device__ cplx *u(int m) const { return U + (m - 1) * NP; }
 
-    // lane-summed ||y||^2 of a synchronised buffer
+    // lane-summed ||y||^2 (y written by this lane on its rows)
     __device__ double norm2(const cplx *y) const
     {
         typename Ar::red nn = Ar::rzero();
@@ -103,8 +124,9 @@ struct Expo {
     // out = P_l x, synchronised; returns ||out||^2
     __device__ double apply_level(int l, const cplx *x, cplx *out)
     {
-        const typename Ar::red p = level_apply<Ar, G, R>(level(l), x, out, g.gl, a.n);
-        const double nn = Ar::rval(Ar::rsum(g, p));
+        typename Ar::red p[1];
+        level_apply<Ar, G, R, 1>(level(l), x, out, g.gl, a.n, p);
+        const double nn = Ar::rval(Ar::rsum(g, p[0]));
         g.sync();
         ++n_rhs;
         return nn;
@@ -138,7 +160,8 @@ struct Expo {
     }
 
     // exp(d M) psi: the binary digits of d / delta on the ladder, then the
-    // remainder by Taylor.  Returns the buffer holding the result (never psi).
+    // remainder by Taylor.  Returns the buffer holding the result (A, B, u_1 or
+    // u_2; never psi).
     __device__ cplx *propagate(double d, const cplx *psi)
     {
         const int L = a.expo_levels - 1;
@@ -157,7 +180,6 @@ struct Expo {
             }
         }
         const unsigned long long q = (unsigned long long)qd;
-        cplx *A = slot(kEA), *B = slot(kEB);
         const cplx *cur = psi;
 #pragma unroll 1
         for (int l = L; l >= 0; --l)
@@ -166,8 +188,8 @@ struct Expo {
                 apply_level(l, cur, out);
                 cur = out;
             }
-        if (rem > 0.0) return taylor(cur, slot(kEU), slot(kEU + 1), rem);
-        if (cur == psi) {  // d == 0: a copy, so that the caller may overwrite psi
+        if (rem > 0.0) return taylor(cur, u(1), u(2), rem);
+        if (cur == psi) {  // d == 0: a copy
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int row = g.gl + G * r;
@@ -180,12 +202,11 @@ struct Expo {
     }
 
     // (B) with ||psi||^2 = nb >= r now and ||exp(d M) psi||^2 < r: the time s in
-    // (0, d] of the crossing; psi(s) is left in *out (synchronised).
+    // (0, d] of the crossing; psi(s) is left in *out (A or B, synchronised).
     __device__ double crossing(double d, const cplx *psi, double nb, double r, double t0, cplx **out)
     {
         const int L = a.expo_levels - 1;
         const double delta = a.expo_delta;
-        cplx *A = slot(kEA), *B = slot(kEB);
         const cplx *base = psi;
         double cur = 0.0;
         // binary descent: keep level l when the norm after it is still >= r
@@ -210,7 +231,7 @@ struct Expo {
         const cplx *prev = base;
 #pragma unroll 1
         for (int m = 1; m <= kExpoTaylor; ++m) {
-            cplx *um = slot(kEU + m - 1);
+            cplx *um = u(m);
             const typename Ar::coef inv = Ar::coef_of(1.0 / m);
 #pragma unroll 1
             for (int r2 = 0; r2 < R; ++r2) {
@@ -237,7 +258,7 @@ struct Expo {
                     double sp = 1.0;  // s^(m-1)
 #pragma unroll
                     for (int m = 1; m <= kExpoTaylor; ++m) {
-                        const cplx um = slot(kEU + m - 1)[row];
+                        const cplx um = u(m)[row];
                         Ar::axpy(yp, Ar::coef_of(m * sp), um);
                         sp *= s;
                         Ar::axpy(y, Ar::coef_of(sp), um);
@@ -289,7 +310,7 @@ struct Expo {
 #pragma unroll
                 for (int m = 1; m <= kExpoTaylor; ++m) {
                     sp *= s;
-                    Ar::axpy(y, Ar::coef_of(sp), slot(kEU + m - 1)[row]);
+                    Ar::axpy(y, Ar::coef_of(sp), u(m)[row]);
                 }
                 o[row] = Ar::add_scaled(base[row], Ar::coef_of(1.0), y);
             }
@@ -300,122 +321,172 @@ struct Expo {
     }
 };
 
-template <class Ar, int G, int R>
-__device__ void run_trajectory_expo(const KernelArgs &a, const Group<G> &g, const int *si,
-                                    const typename Ar::real *sv, typename Ar::cplx *slots, long long il)
+// Per-trajectory scalars of a group (indexed at run time; they live in local memory).
+struct ExpoTraj {
+    double t, r, c, nb;
+    long long k, steps;
+    int status, jdone;
+    unsigned long long n_jump;
+};
+
+// Trajectories il0 .. il0 + live - 1 (live <= T) of the launch, in lock step.
+template <class Ar, int G, int R, int T>
+__device__ void run_group_expo(const KernelArgs &a, const Group<G> &g, const int *si, const typename Ar::real *sv,
+                               typename Ar::cplx *slots, long long il0, int live)
 {
     using cplx = typename Ar::cplx;
+    using S = ExpoSlots<T>;
     constexpr int NP = G * R;
     const int n = a.n, gl = g.gl;
-    const long long traj = a.traj0 + il;
-    double *out = a.out + (size_t)il * a.n_t * a.n_obs;
-    Expo<Ar, G, R> E{a, g, csr_view<Ar>(a.op[0], si, sv), slots};
-    Lanes<Ar, G, R> L{slots, gl, n, 0};
-    cplx *psi = slots + kEPsi * NP;
-    cplx *A = slots + kEA * NP;
+    Expo<Ar, G, R> E{a, g, csr_view<Ar>(a.op[0], si, sv), slots + S::kA * NP, slots + S::kB * NP,
+                     slots + S::kU * NP};
+    cplx *psi_all = slots + S::kPsi * NP;
+    cplx *y_all = slots + S::kY * NP;
+    ExpoTraj tr[T];
+    unsigned long long n_acc = 0;
 
-    int status = 0;
-    unsigned long long n_acc = 0, n_jump = 0;
-    long long steps = 0;
-
-    // (A)
+    // (A): psi0 for the live trajectories, zero in the unused slots
     const cplx *psi0 = static_cast<const cplx *>(a.psi0);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int row = gl + G * r;
-        if (row < n) psi[row] = psi0[row];
-    }
+    for (int t = 0; t < T; ++t)
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int row = gl + G * r;
+            if (row < n) psi_all[t * NP + row] = t < live ? psi0[row] : Ar::czero();
+        }
     g.sync();
-    long long k = 0;
-    double rk, ck;
-    jump_draws(a.seed, traj, k, rk, ck);
-    double t = a.t[0];
-    record_outputs<Ar, G, R>(a, g, si, sv, psi, 0, out, nullptr);
-    double nb = E.norm2(psi);
-    bool at_grid = true;
-    int j = 1;
-    while (j < a.n_t) {
-        if (++steps > a.max_steps) {
-            status = 4;
-            break;
+#pragma unroll 1
+    for (int t = 0; t < live; ++t) {
+        ExpoTraj &x = tr[t];
+        x.k = 0;
+        jump_draws(a.seed, a.traj0 + il0 + t, 0, x.r, x.c);
+        x.t = a.t[0];
+        x.steps = 0;
+        x.status = 0;
+        x.jdone = a.n_t;
+        x.n_jump = 0;
+        record_outputs<Ar, G, R>(a, g, si, sv, psi_all + t * NP, 0, a.out + (size_t)(il0 + t) * a.n_t * a.n_obs,
+                                 nullptr);
+        x.nb = E.norm2(psi_all + t * NP);
+    }
+#pragma unroll 1
+    for (int j = 1; j < a.n_t; ++j) {
+        typename Ar::red part[T];
+        if (a.expo_uniform) {
+            level_apply<Ar, G, R, T>(E.level(a.expo_levels - 1), psi_all, y_all, gl, n, part);
+            g.sync();
         }
-        const double d = a.t[j] - t;
-        cplx *y;
-        double nn;
-        if (a.expo_uniform && at_grid) {
-            y = A;
-            nn = E.apply_level(a.expo_levels - 1, psi, A);
-        } else {
-            y = E.propagate(d, psi);
-            nn = E.norm2(y);
-        }
-        if (!isfinite(nn)) {
-            status = 6;
-            break;
-        }
-        if (nn >= rk) {
-            record_outputs<Ar, G, R>(a, g, si, sv, y, j, out, nullptr);
+        bool any = false;
+#pragma unroll 1
+        for (int t = 0; t < live; ++t) {
+            ExpoTraj &x = tr[t];
+            if (x.status != 0) continue;
+            any = true;
+            cplx *psi = psi_all + t * NP;
+            cplx *y;
+            double nn;
+            ++x.steps;
+            if (a.expo_uniform) {
+                y = y_all + t * NP;
+                typename Ar::red p = Ar::rzero();
+#pragma unroll
+                for (int q = 0; q < T; ++q)
+                    if (q == t) p = part[q];
+                nn = Ar::rval(Ar::rsum(g, p));
+                ++E.n_rhs;
+            } else {
+                y = E.propagate(a.t[j] - x.t, psi);
+                nn = E.norm2(y);
+            }
+            for (;;) {
+                if (!isfinite(nn)) {
+                    x.status = 6;
+                    break;
+                }
+                if (nn >= x.r) break;
+                if (++x.steps > a.max_steps) {
+                    x.status = 4;
+                    break;
+                }
+                // (B): the norm reaches r inside (x.t, t_j]
+                cplx *ytau = nullptr;
+                const double s = E.crossing(a.t[j] - x.t, psi, x.nb, x.r, x.t, &ytau);
+                double tau = x.t + s;
+                if (tau > a.t[j]) tau = a.t[j];
+                // (C)
+                const int ch = apply_jump<Ar, G, R>(a, g, si, sv, psi, E.u(1), ytau, x.c);
+                if (ch < 0) {
+                    x.status = 7;
+                    break;
+                }
+                g.sync();
+                if (gl == 0 && (long long)x.n_jump < a.max_jumps) {
+                    a.jump_t[(size_t)(il0 + t) * a.max_jumps + x.n_jump] = tau;
+                    a.jump_ch[(size_t)(il0 + t) * a.max_jumps + x.n_jump] = ch;
+                }
+                ++x.n_jump;
+                ++n_acc;
+                // (D), then on to t_j
+                ++x.k;
+                jump_draws(a.seed, a.traj0 + il0 + t, x.k, x.r, x.c);
+                x.t = tau;
+                x.nb = 1.0;
+                y = E.propagate(a.t[j] - tau, psi);
+                nn = E.norm2(y);
+            }
+            if (x.status != 0) {
+                x.jdone = j;
+                continue;
+            }
+            record_outputs<Ar, G, R>(a, g, si, sv, y, j, a.out + (size_t)(il0 + t) * a.n_t * a.n_obs, nullptr);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int row = gl + G * r;
                 if (row < n) psi[row] = y[row];
             }
             g.sync();
-            nb = nn;
-            t = a.t[j];
-            ++j;
+            x.nb = nn;
+            x.t = a.t[j];
             ++n_acc;
-            at_grid = true;
-            continue;
         }
-        // (B): the norm reaches r inside (t, t_j]
-        cplx *ytau = nullptr;
-        const double s = E.crossing(d, psi, nb, rk, t, &ytau);
-        double tau = t + s;
-        if (tau > a.t[j]) tau = a.t[j];
-        // (C)
-        const int ch = apply_jump<Ar, G, R>(a, g, si, sv, L, ytau, ck);
-        if (ch < 0) {
-            status = 7;
-            break;
-        }
-        g.sync();
-        if (gl == 0 && (long long)n_jump < a.max_jumps) {
-            a.jump_t[(size_t)il * a.max_jumps + n_jump] = tau;
-            a.jump_ch[(size_t)il * a.max_jumps + n_jump] = ch;
-        }
-        ++n_jump;
-        ++n_acc;
-        // (D)
-        ++k;
-        jump_draws(a.seed, traj, k, rk, ck);
-        t = tau;
-        nb = 1.0;
-        at_grid = false;
+        if (!any) break;
     }
 
     if (gl == 0) {
-        if (status != 0) {
-            for (; j < a.n_t; ++j)
-                for (int q = 0; q < a.n_obs; ++q)
-                    out[(size_t)j * a.n_obs + q] = __longlong_as_double(0x7ff8000000000000LL);
-            atomicCAS(a.first_error, 0, status);
-            atomicAdd(&a.counters[kFailed], 1ULL);
+        unsigned long long jumps = 0;
+        for (int t = 0; t < live; ++t) {
+            const ExpoTraj &x = tr[t];
+            const long long il = il0 + t;
+            if (x.status != 0) {
+                double *out = a.out + (size_t)il * a.n_t * a.n_obs;
+                for (int j = x.jdone; j < a.n_t; ++j)
+                    for (int q = 0; q < a.n_obs; ++q)
+                        out[(size_t)j * a.n_obs + q] = __longlong_as_double(0x7ff8000000000000LL);
+                atomicCAS(a.first_error, 0, x.status);
+                atomicAdd(&a.counters[kFailed], 1ULL);
+            }
+            if (a.max_jumps > 0) a.n_jumps[il] = (int)x.n_jump;
+            jumps += x.n_jump;
         }
-        if (a.max_jumps > 0) a.n_jumps[il] = (int)n_jump;
         atomicAdd(&a.counters[kAccepted], n_acc);
         atomicAdd(&a.counters[kRejected], E.n_rej);
         atomicAdd(&a.counters[kRhs], E.n_rhs);
-        atomicAdd(&a.counters[kJumps], n_jump);
+        atomicAdd(&a.counters[kJumps], jumps);
         atomicAdd(&a.counters[kRootIters], (unsigned long long)E.root_iters);
     }
 }
+
+// Trajectories per group: four with two rows per lane, two with four (the
+// batched product keeps T R accumulators per lane).
+template <int R>
+__host__ __device__ constexpr int expo_batch() { return R == 2 ? 4 : 2; }
 
 template <class Ar, int G, int R, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 1)) mcwf_expo_kernel(const __grid_constant__ KernelArgs a)
 {
     using cplx = typename Ar::cplx;
     using real = typename Ar::real;
+    constexpr int T = expo_batch<R>();
     extern __shared__ __align__(16) unsigned char smem[];
     const int *si;
     const real *sv;
@@ -433,13 +504,15 @@ __global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 1)) mcwf_expo_kernel(con
     }
     __syncthreads();
     const Group<G> g(threadIdx.x, reinterpret_cast<unsigned long long *>(smem + a.smem_scratch_offset));
-    cplx *slots = reinterpret_cast<cplx *>(smem + a.smem_ybuf_offset) + (threadIdx.x / G) * kNumExpoSlots * (G * R);
+    cplx *slots = reinterpret_cast<cplx *>(smem + a.smem_ybuf_offset) +
+                  (size_t)(threadIdx.x / G) * ExpoSlots<T>::kCount * (G * R);
     for (;;) {
         unsigned long long i = 0;
-        if (g.gl == 0) i = atomicAdd(a.queue, 1ULL);
+        if (g.gl == 0) i = atomicAdd(a.queue, (unsigned long long)T);
         i = g.bcast0(i);
         if ((long long)i >= a.ntraj) break;
-        run_trajectory_expo<Ar, G, R>(a, g, si, sv, slots, (long long)i);
+        const long long left = a.ntraj - (long long)i;
+        run_group_expo<Ar, G, R, T>(a, g, si, sv, slots, (long long)i, left < T ? (int)left : T);
     }
 }
 
@@ -449,6 +522,7 @@ cudaError_t launch_expo_instance(const KernelArgs &a0, cudaStream_t stream, Laun
     using cplx = typename Ar::cplx;
     constexpr int BLOCK = block_for_group<G>();
     constexpr int GROUPS = BLOCK / G;
+    constexpr int T = expo_batch<R>();
     KernelArgs a = a0;
     auto al16 = [](size_t x) { return (x + 15) & ~size_t(15); };
     const size_t ib = ops_in_shared<G>() ? al16((size_t)a.n_ints * sizeof(int)) : 0;
@@ -457,7 +531,7 @@ cudaError_t launch_expo_instance(const KernelArgs &a0, cudaStream_t stream, Laun
     a.smem_vals_offset = (int)ib;
     a.smem_scratch_offset = (int)(ib + vb);
     a.smem_ybuf_offset = (int)(ib + vb + sb);
-    const size_t smem = ib + vb + sb + (size_t)GROUPS * kNumExpoSlots * G * R * sizeof(cplx);
+    const size_t smem = ib + vb + sb + (size_t)GROUPS * ExpoSlots<T>::kCount * G * R * sizeof(cplx);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     auto kern = mcwf_expo_kernel<Ar, G, R, BLOCK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -467,7 +541,7 @@ cudaError_t launch_expo_instance(const KernelArgs &a0, cudaStream_t stream, Laun
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, BLOCK, smem)) != cudaSuccess) return e;
     if (nb < 1) nb = 1;
-    const long long need = (a.ntraj + GROUPS - 1) / GROUPS;
+    const long long need = (a.ntraj + (long long)GROUPS * T - 1) / ((long long)GROUPS * T);
     long long grid = (long long)nb * sms;
     if (need < grid) grid = need < 1 ? 1 : need;
     kern<<<(unsigned)grid, BLOCK, smem, stream>>>(a);

@@ -401,25 +401,25 @@ __device__ __noinline__ double locate_crossing(const Coefs<Ar> &C, Lanes<Ar, G, 
     return x;
 }
 
-// Step (C) after the crossing time is known: y = psi(tau) is in the exchange half
-// `y` (group synchronised).  Chooses the channel, writes C_n* y / ||C_n* y|| to
-// the psi slot, and returns the channel (or -1 when every weight is zero).
+// Step (C) after the crossing time is known: y = psi(tau) is in a shared-memory
+// vector (group synchronised).  Chooses the channel, writes C_n* y / ||C_n* y||
+// to psi (lane rows; tmp is lane-row scratch), and returns the channel (or -1
+// when every weight is zero).
 template <class Ar, int G, int R>
 __device__ __noinline__ int apply_jump(const KernelArgs &a, Group<G> g, const int *si,
-                                       const typename Ar::real *sv, Lanes<Ar, G, R> L,
-                                       const typename Ar::cplx *y, double ck)
+                                       const typename Ar::real *sv, typename Ar::cplx *psi,
+                                       typename Ar::cplx *tmp, const typename Ar::cplx *y, double ck)
 {
-    using cplx = typename Ar::cplx;
+    const int gl = g.gl, n = a.n;
     double wq[kMaxChannels];
     double wsum = 0.0;
-    cplx *tmp = L.slot(kYn);  // ynew (in K_1's slot) is dead after a crossing
     for (int q = 0; q < a.n_c; ++q) {
-        spmv_rows<Ar, G, R>(csr_view<Ar>(a.op[1 + q], si, sv), y, tmp, L.gl, L.n);
+        spmv_rows<Ar, G, R>(csr_view<Ar>(a.op[1 + q], si, sv), y, tmp, gl, n);
         typename Ar::red part = Ar::rzero();
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const int row = L.gl + G * r;
-            if (row < L.n) part = Ar::radd(part, Ar::abs2(tmp[row]));
+            const int row = gl + G * r;
+            if (row < n) part = Ar::radd(part, Ar::abs2(tmp[row]));
         }
         wq[q] = Ar::rval(Ar::rsum(g, part));
         wsum += wq[q];
@@ -435,13 +435,12 @@ __device__ __noinline__ int apply_jump(const KernelArgs &a, Group<G> g, const in
             break;
         }
     }
-    cplx *psi = L.slot(kPsi);
-    spmv_rows<Ar, G, R>(csr_view<Ar>(a.op[1 + ch], si, sv), y, psi, L.gl, L.n);
+    spmv_rows<Ar, G, R>(csr_view<Ar>(a.op[1 + ch], si, sv), y, psi, gl, n);
     const double nc = sqrt(wq[ch]);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-        const int row = L.gl + G * r;
-        if (row < L.n) psi[row] = Ar::div(psi[row], nc);
+        const int row = gl + G * r;
+        if (row < n) psi[row] = Ar::div(psi[row], nc);
     }
     return ch;
 }
@@ -712,7 +711,8 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
             b = L.xnext();
             dense_rows<Ar, G, R>(C, L, h, th, b);
             g.sync();
-            const int ch = apply_jump<Ar, G, R>(a, g, si, sv, L, b, ck);
+            // ynew (in K_1's slot) is dead after a crossing: it serves as scratch
+            const int ch = apply_jump<Ar, G, R>(a, g, si, sv, L.slot(kPsi), L.slot(kYn), b, ck);
             if (ch < 0) {
                 status = 7;
                 break;
