@@ -7,11 +7,11 @@
 // The host precomputes a ladder of propagators P_l = exp(M delta 2^l),
 // l = 0..L, with delta chosen so that nu delta <= 1/16 (nu >= ||M||_2) and
 // delta 2^L = the output spacing.  A group of G lanes (R rows per lane, vectors
-// in shared memory as in mcwf_kernel.cuh) carries T trajectories in lock step
-// from output to output:
-//   * between outputs: psi_t(t_j) = P_L psi_t(t_{j-1}) for all T trajectories in
-//     one pass over P_L on a uniform grid (each column of P_L loaded once for T
-//     products); otherwise, per trajectory, the duration d is split into its binary digits in
+// in shared memory as in mcwf_kernel.cuh) carries T trajectories (see
+// expo_batch) in lock step from output to output:
+//   * between outputs: psi_t(t_j) = P_L psi_t(t_{j-1}) for the group's
+//     trajectories in one pass over P_L on a uniform grid; otherwise, per
+//     trajectory, the duration d is split into its binary digits in
 //     units of delta (one product per digit) and a remainder s < delta, which
 //     takes a degree-9 Taylor polynomial of exp(s M) (9 products with M; the
 //     truncation error is below 3e-19 relative);
@@ -62,7 +62,10 @@ __device__ __forceinline__ void level_apply(const typename Ar::cplx *__restrict_
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[t][r] = Ar::zero();
     const typename Ar::cplx *col = P + gl;
-#pragma unroll 2
+    // columns in flight: four, or two where the accumulators already fill the
+    // registers (double-float, batches)
+    constexpr int kUnroll = (T > 1 || Ar::kId == ArDF::kId) ? 2 : 4;
+#pragma unroll(kUnroll)
     for (int c = 0; c < n; ++c) {
         typename Ar::cplx p[R];
 #pragma unroll
@@ -476,13 +479,20 @@ __device__ void run_group_expo(const KernelArgs &a, const Group<G> &g, const int
     }
 }
 
-// Trajectories per group: four with two rows per lane, two with four (the
-// batched product keeps T R accumulators per lane).
+// Trajectories per group.  Lock-step batches (one pass over P_L for T
+// trajectories) were measured with T = 4 (two rows per lane) and T = 2 (four):
+// 8 % faster on dense N = 256 in double-float, but slower everywhere else
+// (dense complex64 -43 %, the stiff system -24 %, Jaynes-Cummings -8 to -21 %),
+// because each trajectory's outputs, reductions and jumps then run one after
+// another inside the group while fewer groups share an SM.  One trajectory per
+// group is kept.
 template <int R>
-__host__ __device__ constexpr int expo_batch() { return R == 2 ? 4 : 2; }
+__host__ __device__ constexpr int expo_batch() { return 1; }
 
+// Multi-warp groups: two CTAs per SM (the register bound keeps a second CTA
+// resident; one CTA per SM halved the dense complex64 throughput).
 template <class Ar, int G, int R, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 1)) mcwf_expo_kernel(const __grid_constant__ KernelArgs a)
+__global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 2)) mcwf_expo_kernel(const __grid_constant__ KernelArgs a)
 {
     using cplx = typename Ar::cplx;
     using real = typename Ar::real;
