@@ -74,7 +74,7 @@ def parse():
                     help="skip the exponential-method legs (stiff Purcell system, Jaynes-Cummings)")
     ap.add_argument("--no-ising", action="store_true",
                     help="skip the batched Ising-chain measurement (L = 6..10 in one CUDA graph)")
-    ap.add_argument("--only", choices=["c128", "df64", "c64", "dense", "expo_purcell", "expo_jc"], default=None,
+    ap.add_argument("--only", choices=["c128", "df64", "c64", "dense", "expo_purcell", "expo_jc", "expo_dense"], default=None,
                     help="time one arithmetic only (profiling); no observable-error comparison.  'dense': the "
                          "tensor-core engine on the dense N = 256 system with --ntraj trajectories")
     ap.add_argument("--dense-t-end", type=float, default=10.0, help="--only dense: end of the time grid")
@@ -380,11 +380,12 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return 0
-    if args.only in ("expo_purcell", "expo_jc"):
+    if args.only in ("expo_purcell", "expo_jc", "expo_dense"):
         from paper_1810_03047_gb300 import systems as S
-        eprob = S.purcell_qubit(ntraj=args.ntraj) if args.only == "expo_purcell" else prob
+        eprob = {"expo_purcell": S.purcell_qubit(ntraj=args.ntraj), "expo_jc": prob,
+                 "expo_dense": S.dense_random(ntraj=args.ntraj)}[args.only]
         res = {}
-        for pname, prec in (("c128", Q.QTM_PREC_C128), ("df64", Q.QTM_PREC_DF64)):
+        for pname, prec in (("c128", Q.QTM_PREC_C128), ("df64", Q.QTM_PREC_DF64), ("c64", Q.QTM_PREC_C64)):
             res[pname] = _timed_passes(Q, torch, stream, world, dist, eprob, prec, Q.QTM_METHOD_EXPONENTIAL, first,
                                        ntraj, passes=max(1, args.steps))
         clk = clocks.stop()
@@ -395,7 +396,8 @@ def main():
                               "data": "synthetic", "config": {"workload": eprob.name, "ntraj_per_gpu": ntraj,
                                                               "method": "exponential"},
                               "df64": {k: v for k, v in res["df64"].items() if k != "mean"},
-                              "gpu_launches": res["c128"]["launches"] + res["df64"]["launches"], "clocks": clk,
+                              "c64": {k: v for k, v in res["c64"].items() if k != "mean"},
+                              "gpu_launches": sum(r["launches"] for r in res.values()), "clocks": clk,
                               "note": "exponential method only (profiling run)"}), flush=True)
         if world > 1:
             dist.destroy_process_group()
