@@ -103,6 +103,7 @@ struct Expo {
     const Group<G> &g;
     CsrView<Ar> M;
     cplx *A, *B, *U;
+    const typename Ar::coef *inv;  // inv[m] = 1/m in the coefficient type (shared memory)
     unsigned long long n_rhs = 0, n_rej = 0;
     int root_iters = 0;
 
@@ -141,9 +142,10 @@ struct Expo {
     {
         const cplx *src = x;
         cplx *dst = w0;
+        const typename Ar::coef sc = Ar::coef_of(s);
 #pragma unroll 1
         for (int m = kExpoTaylor; m >= 1; --m) {
-            const typename Ar::coef sm = Ar::coef_of(s / m);
+            const typename Ar::coef sm = Ar::cmul(sc, inv[m]);
 #pragma unroll 1
             for (int r = 0; r < R; ++r) {
                 const cplx mv = spmv_row<Ar, G>(M, src, g.gl, r);
@@ -235,14 +237,14 @@ struct Expo {
 #pragma unroll 1
         for (int m = 1; m <= kExpoTaylor; ++m) {
             cplx *um = u(m);
-            const typename Ar::coef inv = Ar::coef_of(1.0 / m);
+            const typename Ar::coef im = inv[m];
 #pragma unroll 1
             for (int r2 = 0; r2 < R; ++r2) {
                 const cplx mv = spmv_row<Ar, G>(M, prev, g.gl, r2);
                 const int row = g.gl + G * r2;
                 if (row < a.n) {
                     typename Ar::acc acc = Ar::zero();
-                    Ar::axpy(acc, inv, mv);
+                    Ar::axpy(acc, im, mv);
                     um[row] = Ar::get(acc);
                 }
             }
@@ -250,21 +252,29 @@ struct Expo {
             ++n_rhs;
             prev = um;
         }
-        // f(s) = ||sum_m s^m u_m||^2 - r and f'(s) = 2 Re<psi(s), psi'(s)>
+        // f(s) = ||sum_m s^m u_m||^2 - r and f'(s) = 2 Re<psi(s), psi'(s)>; the
+        // powers are formed once per evaluation in the arithmetic's coefficient
+        // type (FP32 pairs or floats on the FP32 pipe, doubles for complex128)
         auto eval = [&](double s, double &fp) {
+            typename Ar::coef pw[kExpoTaylor + 1], dpw[kExpoTaylor + 1];
+            const typename Ar::coef sc = Ar::coef_of(s);
+            pw[0] = Ar::coef_of(1.0);
+#pragma unroll
+            for (int m = 1; m <= kExpoTaylor; ++m) {
+                dpw[m] = Ar::cmul(Ar::cconst((double)m), pw[m - 1]);
+                pw[m] = Ar::cmul(pw[m - 1], sc);
+            }
             typename Ar::red nn = Ar::rzero(), dd = Ar::rzero();
 #pragma unroll 1
             for (int r2 = 0; r2 < R; ++r2) {
                 const int row = g.gl + G * r2;
                 if (row < a.n) {
                     typename Ar::acc y = Ar::zero(), yp = Ar::zero();
-                    double sp = 1.0;  // s^(m-1)
 #pragma unroll
                     for (int m = 1; m <= kExpoTaylor; ++m) {
                         const cplx um = u(m)[row];
-                        Ar::axpy(yp, Ar::coef_of(m * sp), um);
-                        sp *= s;
-                        Ar::axpy(y, Ar::coef_of(sp), um);
+                        Ar::axpy(yp, dpw[m], um);
+                        Ar::axpy(y, pw[m], um);
                     }
                     const cplx yv = Ar::add_scaled(base[row], Ar::coef_of(1.0), y);
                     const cplx ypv = Ar::get(yp);
@@ -304,17 +314,20 @@ struct Expo {
         }
         // psi(s) into the product buffer that does not hold the base
         cplx *o = (base == A) ? B : A;
+        typename Ar::coef pw[kExpoTaylor + 1];
+        {
+            const typename Ar::coef sc = Ar::coef_of(s);
+            pw[0] = Ar::coef_of(1.0);
+#pragma unroll
+            for (int m = 1; m <= kExpoTaylor; ++m) pw[m] = Ar::cmul(pw[m - 1], sc);
+        }
 #pragma unroll 1
         for (int r2 = 0; r2 < R; ++r2) {
             const int row = g.gl + G * r2;
             if (row < a.n) {
                 typename Ar::acc y = Ar::zero();
-                double sp = 1.0;
 #pragma unroll
-                for (int m = 1; m <= kExpoTaylor; ++m) {
-                    sp *= s;
-                    Ar::axpy(y, Ar::coef_of(sp), u(m)[row]);
-                }
+                for (int m = 1; m <= kExpoTaylor; ++m) Ar::axpy(y, pw[m], u(m)[row]);
                 o[row] = Ar::add_scaled(base[row], Ar::coef_of(1.0), y);
             }
         }
@@ -335,14 +348,14 @@ struct ExpoTraj {
 // Trajectories il0 .. il0 + live - 1 (live <= T) of the launch, in lock step.
 template <class Ar, int G, int R, int T>
 __device__ void run_group_expo(const KernelArgs &a, const Group<G> &g, const int *si, const typename Ar::real *sv,
-                               typename Ar::cplx *slots, long long il0, int live)
+                               const typename Ar::coef *inv, typename Ar::cplx *slots, long long il0, int live)
 {
     using cplx = typename Ar::cplx;
     using S = ExpoSlots<T>;
     constexpr int NP = G * R;
     const int n = a.n, gl = g.gl;
     Expo<Ar, G, R> E{a, g, csr_view<Ar>(a.op[0], si, sv), slots + S::kA * NP, slots + S::kB * NP,
-                     slots + S::kU * NP};
+                     slots + S::kU * NP, inv};
     cplx *psi_all = slots + S::kPsi * NP;
     cplx *y_all = slots + S::kY * NP;
     ExpoTraj tr[T];
@@ -512,6 +525,9 @@ __global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 2)) mcwf_expo_kernel(con
         si = a.ints;
         sv = static_cast<const real *>(a.vals);
     }
+    using coef = typename Ar::coef;
+    coef *inv = reinterpret_cast<coef *>(smem + a.smem_coef_offset);
+    if (threadIdx.x <= kExpoTaylor) inv[threadIdx.x] = Ar::coef_of(threadIdx.x ? 1.0 / threadIdx.x : 0.0);
     __syncthreads();
     const Group<G> g(threadIdx.x, reinterpret_cast<unsigned long long *>(smem + a.smem_scratch_offset));
     cplx *slots = reinterpret_cast<cplx *>(smem + a.smem_ybuf_offset) +
@@ -522,7 +538,7 @@ __global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 2)) mcwf_expo_kernel(con
         i = g.bcast0(i);
         if ((long long)i >= a.ntraj) break;
         const long long left = a.ntraj - (long long)i;
-        run_group_expo<Ar, G, R, T>(a, g, si, sv, slots, (long long)i, left < T ? (int)left : T);
+        run_group_expo<Ar, G, R, T>(a, g, si, sv, inv, slots, (long long)i, left < T ? (int)left : T);
     }
 }
 
@@ -538,10 +554,12 @@ cudaError_t launch_expo_instance(const KernelArgs &a0, cudaStream_t stream, Laun
     const size_t ib = ops_in_shared<G>() ? al16((size_t)a.n_ints * sizeof(int)) : 0;
     const size_t vb = ops_in_shared<G>() ? al16((size_t)a.n_vals * sizeof(typename Ar::real)) : 0;
     const size_t sb = al16((size_t)GROUPS * (Group<G>::kWarps + 1) * 8);
+    const size_t cb = al16((kExpoTaylor + 1) * sizeof(typename Ar::coef));
     a.smem_vals_offset = (int)ib;
     a.smem_scratch_offset = (int)(ib + vb);
-    a.smem_ybuf_offset = (int)(ib + vb + sb);
-    const size_t smem = ib + vb + sb + (size_t)GROUPS * ExpoSlots<T>::kCount * G * R * sizeof(cplx);
+    a.smem_coef_offset = (int)(ib + vb + sb);
+    a.smem_ybuf_offset = (int)(ib + vb + sb + cb);
+    const size_t smem = ib + vb + sb + cb + (size_t)GROUPS * ExpoSlots<T>::kCount * G * R * sizeof(cplx);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     auto kern = mcwf_expo_kernel<Ar, G, R, BLOCK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

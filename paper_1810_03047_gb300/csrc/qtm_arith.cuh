@@ -174,6 +174,7 @@ struct ArF64 {
 
     __host__ __device__ static constexpr coef cconst(double x) { return x; }
     __device__ static coef coef_of(double x) { return x; }
+    __device__ static coef cmul(coef x, coef y) { return x * y; }
     __device__ static acc zero() { return acc{0.0, 0.0}; }
     __device__ static cplx czero() { return cplx{0.0, 0.0}; }
     __device__ static void mac(acc &a, cplx x, cplx y)
@@ -268,6 +269,7 @@ struct ArDF {
 
     __host__ __device__ static constexpr coef cconst(double x) { return df_const(x); }
     __device__ static coef coef_of(double x) { return df_from_double(x); }
+    __device__ static coef cmul(coef x, coef y) { return df_mul(x, y); }
     __device__ static acc zero() { return acc{{0.f, 0.f}, {0.f, 0.f}}; }
     __device__ static cplx czero() { return cplx{{0.f, 0.f}, {0.f, 0.f}}; }
     __device__ static void mac(acc &a, cplx x, cplx y)
@@ -379,6 +381,7 @@ struct ArF32 {
 
     __host__ __device__ static constexpr coef cconst(double x) { return (float)x; }
     __device__ static coef coef_of(double x) { return (float)x; }
+    __device__ static coef cmul(coef x, coef y) { return x * y; }
     __device__ static acc zero() { return acc{0.f, 0.f}; }
     __device__ static cplx czero() { return cplx{0.f, 0.f}; }
     __device__ static void mac(acc &a, cplx x, cplx y)
