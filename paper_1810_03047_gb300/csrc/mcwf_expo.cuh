@@ -62,9 +62,11 @@ __device__ __forceinline__ void level_apply(const typename Ar::cplx *__restrict_
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[t][r] = Ar::zero();
     const typename Ar::cplx *col = P + gl;
-    // columns in flight: four, or two where the accumulators already fill the
-    // registers (double-float, batches)
-    constexpr int kUnroll = (T > 1 || Ar::kId == ArDF::kId) ? 2 : 4;
+    // columns in flight: four; two where the accumulators already fill the
+    // registers (double-float, batches); eight for complex64 on multi-warp
+    // groups, whose large P_L streams from L2 (dense N = 256: +6 %; on the
+    // single-warp layouts eight measured 3-4 % slower)
+    constexpr int kUnroll = (T > 1 || Ar::kId == ArDF::kId) ? 2 : (Ar::kId == ArF32::kId && G >= 64 ? 8 : 4);
 #pragma unroll(kUnroll)
     for (int c = 0; c < n; ++c) {
         typename Ar::cplx p[R];
