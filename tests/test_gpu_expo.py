@@ -229,3 +229,23 @@ def test_expo_complex64_statistics(orc, name, kw, ntraj):
     assert g["stats"]["failed"] == 0
     L, _ = orc.lindblad(prob, 1e-10, 1e-12)
     _within_statistics(g["mean"], g["se"], L, ntraj)
+
+
+def test_expo_shards_equal_one_run():
+    """Contiguous id ranges (one per GPU in a multi-GPU run) reproduce one run
+    over all ids bitwise under the exponential method too: every draw is keyed
+    by (seed, global trajectory id)."""
+    from paper_1810_03047_gb300 import shards
+    prob = S.purcell_qubit()
+    n, world = 301, 3
+    ctx = Q.qtm_create(prob, record_jumps=16)
+    Q.qtm_set_method(ctx, Q.QTM_METHOD_EXPONENTIAL)
+    Q.qtm_run(ctx, n, 5)
+    whole = Q.qtm_traj_expect(ctx)
+    parts = []
+    for rank in range(world):
+        first, count = shards.shard(n, world, rank)
+        Q.qtm_run_range(ctx, first, count, 5)
+        parts.append(Q.qtm_traj_expect(ctx))
+    Q.qtm_destroy(ctx)
+    np.testing.assert_array_equal(np.concatenate(parts), whole)
