@@ -499,8 +499,10 @@ __device__ void run_group_expo(const KernelArgs &a, const Group<G> &g, const int
 // 8 % faster on dense N = 256 in double-float, but slower everywhere else
 // (dense complex64 -43 %, the stiff system -24 %, Jaynes-Cummings -8 to -21 %),
 // because each trajectory's outputs, reductions and jumps then run one after
-// another inside the group while fewer groups share an SM.  One trajectory per
-// group is kept.
+// another inside the group while fewer groups share an SM.  With two CTAs per
+// SM restored, T = 2 for complex64 on the multi-warp layouts (dense N = 256)
+// measured the same as one trajectory per group (106k trajectories/s).  One
+// trajectory per group is kept.
 template <int R>
 __host__ __device__ constexpr int expo_batch() { return 1; }
 
