@@ -7,8 +7,9 @@
 // The host precomputes a ladder of propagators P_l = exp(M delta 2^l),
 // l = 0..L, with delta chosen so that nu delta <= 1/16 (nu >= ||M||_2) and
 // delta 2^L = the output spacing.  A group of G lanes (R rows per lane, vectors
-// in shared memory as in mcwf_kernel.cuh) carries T trajectories (see
-// expo_batch) in lock step from output to output:
+// in shared memory as in mcwf_kernel.cuh) carries T trajectories in lock step
+// from output to output (T = 1 in every instantiation, see expo_batch; the code
+// is written for general T):
 //   * between outputs: psi_t(t_j) = P_L psi_t(t_{j-1}) for the group's
 //     trajectories in one pass over P_L on a uniform grid; otherwise, per
 //     trajectory, the duration d is split into its binary digits in
