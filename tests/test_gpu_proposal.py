@@ -69,7 +69,7 @@ def test_network_improves_on_constant_rate_estimate(trained):
 
 
 def test_proposal_keeps_jumps_and_reports_gain(trained, capsys):
-    """The root find still judges: with the proposal on, the same jumps happen at
+    """The root find still decides: with the proposal on, the same jumps happen at
     the same times up to the integration tolerance; only the step sequence changes.
 
     The step count is reported, not required to fall.  With a continuous
