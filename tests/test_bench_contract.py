@@ -25,3 +25,27 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert "workload" in d["config"]
+
+
+import pytest  # noqa: E402
+
+
+@pytest.mark.gpu
+def test_gpu_arm_profiling_line():
+    """A short single-arithmetic run of the GPU arm: one JSON line with the
+    roofline object, the clock record and the launch count."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--only", "df64", "--ntraj", "2000",
+                        "--steps", "1", "--warmup", "1"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [x for x in r.stdout.splitlines() if x.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "gpu_launches", "clocks"):
+        assert key in d, key
+    rl = d["roofline"]
+    assert rl["bound"] == "alu" and rl["unit"] == "TFLOP/s" and 0 < rl["frac"] < 1.5
+    assert abs(rl["frac"] - rl["achieved"] / rl["peak"]) < 1e-12
+    assert rl["traffic"] is None  # traffic is reported for the full-size launch only
+    assert d["gpu_launches"] > 0 and d["value"] > 0
+    assert "sm_mhz" in d["clocks"] and "reasons" in d["clocks"]
