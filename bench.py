@@ -25,6 +25,7 @@ Prints one JSON line (rank 0).
 from __future__ import annotations
 
 import argparse
+import platform
 import json
 import os
 import statistics
@@ -191,9 +192,30 @@ def cpu_baseline(prob, seconds, rank):
     t0 = time.perf_counter()
     r = oracle.mcwf(prob, ntraj=n, nthreads=nthreads, max_jumps=1)
     dt = time.perf_counter() - t0
+    # one core on a smaller sample, for the per-core rate
+    n1 = max(8, min(64, n // max(nthreads, 1)))
+    t1 = time.perf_counter()
+    oracle.mcwf(prob, ntraj=n1, nthreads=1, max_jumps=1)
+    dt1 = time.perf_counter() - t1
     return {"value": n / dt, "unit": UNIT, "cores": nthreads, "kind": "oracle",
             "sample": f"trajectory ids 0..{n - 1} of the same workload ({n} of {prob.ntraj}), "
-                      f"{dt:.1f} s wall on {nthreads} host threads"}
+                      f"{dt:.1f} s wall on {nthreads} host threads",
+            "one_core_value": n1 / dt1, "one_core_sample": f"trajectory ids 0..{n1 - 1} on one thread",
+            "cpu_model": _cpu_model()}
+
+
+def _cpu_model() -> str:
+    """The host CPU's model name (Linux /proc/cpuinfo; Arm cores report their part number)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+    except OSError:
+        return platform.processor() or platform.machine()
+    for key in ("model name", "Model name", "CPU part"):
+        for line in info.splitlines():
+            if line.split(":")[0].strip() == key:
+                return f"{platform.machine()} {key}: {line.split(':', 1)[1].strip()}"
+    return platform.machine()
 
 
 def run_reference(args):
@@ -225,7 +247,8 @@ def run_reference(args):
             "config": {"workload": desc, "ntraj_per_step": per_step,
                        "l2": "n/a (host)", "parallelism": f"{nthreads} host threads"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-                             "sample": f"{per_step} trajectories per step, ids 0..{done - 1}"},
+                             "sample": f"{per_step} trajectories per step, ids 0..{done - 1}",
+                             "cpu_model": _cpu_model()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
