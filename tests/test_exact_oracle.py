@@ -60,7 +60,10 @@ def test_exact_matches_dopri5_oracle_at_tight_tolerance(orc):
     (continuous extension, Newton root find) and the exponential (expm, brentq).
     Same jumps and channels; times and outputs within the integrator's error."""
     from oracle import exact
-    for prob, n in [(S.purcell_qubit(), 30), (S.jaynes_cummings_driven(), 3), (S.two_level_driven(), 40)]:
+    for prob, n in [(S.purcell_qubit(), 30), (S.jaynes_cummings_driven(), 3), (S.two_level_driven(), 40),
+                    (S.paper_photon_birth_death(), 40),      # a creation channel beside the decay
+                    (S.dense_random(N=16, ntraj=12), 12),    # dense operators, four channels
+                    (S.ising_chain(4, ntraj=8), 8)]:         # eight channels
         e = exact.mcwf(prob, ntraj=n)
         d = orc.mcwf(prob.with_(rtol=1e-12, atol=1e-14), ntraj=n)
         assert d["rc"] == 0
