@@ -87,6 +87,9 @@ def lib():
                                               ct.c_double, ct.c_int, ct.c_double,
                                               ct.POINTER(ct.c_double), ct.POINTER(ct.c_double),
                                               ct.POINTER(ct.c_double)]
+            _lib.orc_step_trace.restype = ct.c_int
+            _lib.orc_step_trace.argtypes = [ct.POINTER(OrcProblem), ct.c_uint64, ct.c_int64, ct.c_int64,
+                                            ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]
             _lib.orc_dense_weights.restype = None
             _lib.orc_dense_weights.argtypes = [ct.c_double, ct.POINTER(ct.c_double)]
         return _lib
@@ -198,6 +201,19 @@ def dense_weights(theta: float) -> np.ndarray:
     w = np.zeros(7)
     lib().orc_dense_weights(theta, _dptr(w))
     return w
+
+
+def step_trace(prob, traj: int, seed=None, max_rec: int = 1 << 20):
+    """Every attempted Dormand-Prince step of trajectory `traj`: array of rows
+    (start time, step size, accepted 1 / rejected 0)."""
+    seed = prob.seed if seed is None else seed
+    m = _Marshalled(prob)
+    rec = np.zeros((max_rec, 3))
+    n = ct.c_int64()
+    st = lib().orc_step_trace(ct.byref(m.p), seed, traj, max_rec, _dptr(rec), ct.byref(n))
+    if st:
+        raise RuntimeError(f"orc_step_trace failed: {st}")
+    return rec[:n.value].copy()
 
 
 def mcwf(prob, seed=None, traj0: int = 0, ntraj=None, nthreads=None, max_jumps: int = 64):

@@ -570,6 +570,8 @@ typedef struct {
     double *jump_t, *jump_norm;
     int32_t *jump_ch;
     int64_t counts[4];                /* accepted, rejected, rhs, jumps */
+    double *trace;                    /* test hook: (t, h, accepted) of every attempt, or NULL */
+    int64_t max_trace, n_trace;
 } traj_out;
 
 static int run_trajectory(const model *m, uint64_t seed, int64_t traj, workspace *w, traj_out *o)
@@ -616,6 +618,12 @@ static int run_trajectory(const model *m, uint64_t seed, int64_t traj, workspace
         double err = dp_step(n, model_rhs, &rc, t, w->psi, w->K, h, w->ynew, w->ytmp, rtol, atol);
         rhs += 6;
         attempts++;
+        if (o->trace && o->n_trace < o->max_trace) {
+            double *q = o->trace + 3 * o->n_trace++;
+            q[0] = t;
+            q[1] = h;
+            q[2] = err <= 1.0 ? 1.0 : 0.0;
+        }
         if (!(err <= 1.0)) {
             if (!isfinite(err)) { status = ORC_ERR_NONFINITE; break; }
             double fac = DP_SAFETY * pow(err, -0.2);
@@ -797,6 +805,14 @@ typedef struct {
     int status;
 } worker_arg;
 
+/* the vectors of one trajectory's workspace, carved from 16 n complex values */
+static void workspace_carve(workspace *w, cplx *buf, int n)
+{
+    w->psi = buf; w->ynew = buf + n; w->ytmp = buf + 2 * n; w->yd = buf + 3 * n;
+    w->cy = buf + 4 * n; w->ay = buf + 5 * n; w->dtmp = buf + 15 * n;
+    for (int j = 0; j < 7; j++) w->K[j] = buf + (size_t)(6 + j) * n;
+}
+
 static void *worker(void *varg)
 {
     worker_arg *a = varg;
@@ -806,9 +822,7 @@ static void *worker(void *varg)
     cplx *buf = calloc((size_t)n * 16, sizeof(cplx));
     if (!buf) { a->status = ORC_ERR_NOMEM; return NULL; }
     workspace w;
-    w.psi = buf; w.ynew = buf + n; w.ytmp = buf + 2 * n; w.yd = buf + 3 * n;
-    w.cy = buf + 4 * n; w.ay = buf + 5 * n; w.dtmp = buf + 15 * n;
-    for (int j = 0; j < 7; j++) w.K[j] = buf + (size_t)(6 + j) * n;
+    workspace_carve(&w, buf, n);
     orc_result *res = a->res;
     size_t per = (size_t)p->n_t * p->n_obs;
     for (int64_t i = a->tid; i < a->ntraj; i += a->nthreads) {
@@ -859,6 +873,42 @@ int orc_mcwf(const orc_problem *p, uint64_t seed, int64_t traj0, int64_t ntraj, 
     }
     model_free(&m);
     return first;
+}
+
+/* Test hook: the step sequence of one trajectory.  Runs trajectory `traj` alone
+ * and stores, for each attempted Dormand-Prince step, its start time, its size and
+ * 1 (accepted) or 0 (rejected) in rec[3 i .. 3 i + 2], for at most max_rec
+ * attempts; *n_rec = the number stored.  Observables are computed and dropped. */
+int orc_step_trace(const orc_problem *p, uint64_t seed, int64_t traj, int64_t max_rec, double *rec,
+                   int64_t *n_rec)
+{
+    if (!p || !rec || !n_rec || max_rec < 0 || traj < 0) return ORC_ERR_ARG;
+    if (!(p->rtol > 0.0) || !(p->atol >= 0.0) || p->max_steps <= 0) return ORC_ERR_ARG;
+    model m;
+    int st = model_init(p, &m);
+    if (st) { model_free(&m); return st; }
+    const int n = m.n;
+    cplx *buf = calloc((size_t)n * 16, sizeof(cplx));
+    double *obs = calloc((size_t)p->n_t * (p->n_obs > 0 ? p->n_obs : 1), sizeof(double));
+    if (!buf || !obs) {
+        free(buf);
+        free(obs);
+        model_free(&m);
+        return ORC_ERR_NOMEM;
+    }
+    workspace w;
+    workspace_carve(&w, buf, n);
+    traj_out o;
+    memset(&o, 0, sizeof(o));
+    o.obs_re = obs;
+    o.trace = rec;
+    o.max_trace = max_rec;
+    st = run_trajectory(&m, seed, traj, &w, &o);
+    *n_rec = o.n_trace;
+    free(buf);
+    free(obs);
+    model_free(&m);
+    return st;
 }
 
 /* ---------------------------------------------------------------------------
