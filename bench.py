@@ -3,7 +3,9 @@
 One step = one pass of the whole path over one batch: the trajectory kernel
 (Algorithm 1 of the QTM paper for every trajectory of the batch, with its
 Dormand-Prince integration, jump location, channel choice and observables) plus
-the FP64 ensemble reduction, on inputs already resident in device memory.
+the exact ensemble reduction (integer sums of the quantised values, from which
+the FP64 mean and standard error follow), on inputs already resident in device
+memory.
 
 Default workload: the damped, driven Jaynes-Cummings model (cavity Fock cutoff
 30 x qubit, N = 60, two collapse operators, 401 output times over t in [0, 40],
@@ -13,8 +15,9 @@ complex128 (the plain FP64 GPU path, whose means are the reference), the
 double-float path (FP64-class precision on the FP32 pipe) and complex64; the
 headline `value` is the fastest path whose ensemble stays within 1e-5 of the
 complex128 means.  Under torchrun each rank runs
-its own 20,000 trajectory ids (weak scaling); the FP64 sums are combined with one
-all-reduce per step.
+its own 20,000 trajectory ids (weak scaling); the shards' exact moment words are
+combined with one integer all-reduce per step (exact, so independent of the
+collective's order).
 
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead (the
 reference arm: there is no reference implementation to run, only the paper).
@@ -42,6 +45,9 @@ if ROOT not in sys.path:
 
 METRIC = "trajectories/sec at ≤1e-5 observable error vs plain FP64 GPU path; roofline %"
 UNIT = "trajectories/s"
+# kernels per qtm_run: the trajectory kernel and the two exact-moment kernels of
+# the ensemble reduction
+RUN_LAUNCHES = 3
 
 # DRAM bytes (read + write) of one launch at full size, from one ncu capture with
 # `--metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
@@ -306,7 +312,7 @@ def main():
     stream = torch.cuda.current_stream()
     Q.use_torch_allocator()
     P = len(prob.t) * len(prob.A)
-    sums = torch.zeros(2 * P, dtype=torch.float64, device=dev)
+    words = torch.zeros((P, Q.QTM_MOMENT_WORDS), dtype=torch.int64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
     F = flops_per_attempt(prob.dim, nnz_m)
     pk = peaks()
@@ -314,14 +320,15 @@ def main():
 
     def timed(prec_name, steps, warmup):
         """Times `steps` passes of the path (trajectory kernel + ensemble reduction,
-        plus the all-reduce of the sums across GPUs) with L2 flushed in between."""
+        plus the integer all-reduce of the moment words across GPUs) with L2
+        flushed in between."""
         ctx = Q.qtm_create(prob, stream=int(stream.cuda_stream), precision=codes[prec_name])
 
         def step():
             Q.qtm_run_range(ctx, first, ntraj, prob.seed)
             if world > 1:
-                Q.qtm_sums_device(ctx, sums.data_ptr(), sums.data_ptr() + 8 * P)
-                dist.all_reduce(sums)
+                Q.qtm_moments_device(ctx, words.data_ptr())
+                dist.all_reduce(words)
 
         for _ in range(max(warmup, 0)):
             step()
@@ -344,7 +351,7 @@ def main():
             st = Q.qtm_stats(ctx)
             kernel_ms.append(st["kernel_ms"])
             attempts += st["accepted"] + st["rejected"]
-            launches += 5  # trajectory kernel + four ensemble-reduction kernels
+            launches += RUN_LAUNCHES
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -353,6 +360,10 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
         mean, se = Q.qtm_expect(ctx)
+        if world > 1:  # the whole job's ensemble from the all-reduced words of the last step
+            E = Q.qtm_moments(ctx)[2]
+            m_all = Q.qtm_combine_moments(words.cpu().numpy(), [world * ntraj], len(prob.A), E)[0]
+            mean = m_all.reshape(mean.shape)
         last = Q.qtm_stats(ctx)
         Q.qtm_destroy(ctx)
         kern = sum(kernel_ms) / len(kernel_ms)
@@ -398,7 +409,7 @@ def main():
                               "config": {"workload": f"dense random N=256, t in [0, {args.dense_t_end}], "
                                                      f"{args.dense_outputs} outputs", "ntraj_per_gpu": ntraj},
                               "steps_per_trajectory": (st["accepted"] + st["rejected"]) / ntraj,
-                              "gpu_launches": 5 * (args.steps + max(args.warmup, 0)), "clocks": clk,
+                              "gpu_launches": RUN_LAUNCHES * (args.steps + max(args.warmup, 0)), "clocks": clk,
                               "note": "tensor-core engine only (profiling run)"}), flush=True)
         if world > 1:
             dist.destroy_process_group()
@@ -469,7 +480,7 @@ def main():
     e2e_s = float(te.item())
     h2d = (sum((m.indptr.nbytes // 2 + m.indices.nbytes // 2 + m.data.nbytes) for m in [prob.H] + prob.C + prob.A)
            + prob.psi0.nbytes + prob.t.nbytes)
-    d2h = 2 * P * 8 + 4
+    d2h = P * Q.QTM_MOMENT_WORDS * 8 + 4  # qtm_expect reads the moment words and the first-error code
 
     def side(r, err):
         return {"value": r["value"], "ms_per_step": r["ms_per_step"], "observable_error": err,
@@ -563,7 +574,7 @@ def ising_batch(Q, torch, stream, world, rank, dist):
                         "dephasing 0.02 per site), 50k/20k/10k/5k/2k trajectories, 201 outputs on [0,20], "
                         "one CUDA-graph launch", "precision": "df64",
             "value": world * sum(counts) / (float(t.item()) / 1e3), "unit": UNIT, "ms_per_step": float(t.item()),
-            "observable_error": err, "layouts": [list(x) for x in layouts], "launches": 2 * 5 * 5}
+            "observable_error": err, "layouts": [list(x) for x in layouts], "launches": 2 * 5 * RUN_LAUNCHES}
 
 
 def paper_workloads(Q, torch, stream, world, rank, dist):
@@ -609,7 +620,7 @@ def paper_workloads(Q, torch, stream, world, rank, dist):
                 dist.all_reduce(t, op=dist.ReduceOp.MAX)
             res[pname] = {"e2e_s": float(t.item()), "kernel_ms": st["kernel_ms"],
                           "value": world * count / float(t.item()), "mean": mean}
-            launches += 2 * 5
+            launches += 2 * RUN_LAUNCHES
         out[name] = {"ntraj": world * count, "unit": UNIT,
                      "df64": {k: v for k, v in res["df64"].items() if k != "mean"},
                      "c128": {k: v for k, v in res["c128"].items() if k != "mean"},
@@ -685,7 +696,7 @@ def dense_tensor_core(Q, torch, stream, world, rank, dist, pk, ntraj=20000, samp
                          "traffic": TRAFFIC_PER_LAUNCH["qtm::dense_tc_kernel<256>"] if count == 20000 else None,
                          "kernel": "qtm::dense_tc_kernel<256>",
                          "bytes_per_attempt": bytes_per_attempt, "peak_note": note, "kernel_ms": kms},
-            "launches": 3 * 5 + 5}
+            "launches": 4 * RUN_LAUNCHES}
 
 
 def _timed_passes(Q, torch, stream, world, dist, prob, prec, method, first, count, passes=2):
@@ -715,7 +726,7 @@ def _timed_passes(Q, torch, stream, world, dist, prob, prec, method, first, coun
     Q.qtm_destroy(ctx)
     return {"value": world * count / (float(t.item()) / 1e3), "ms_per_step": float(t.item()),
             "kernel_ms": st["kernel_ms"], "products_per_trajectory": st["rhs_evals"] / count,
-            "jumps_per_trajectory": st["jumps"] / count, "mean": mean, "launches": (1 + passes) * 5}
+            "jumps_per_trajectory": st["jumps"] / count, "mean": mean, "launches": (1 + passes) * RUN_LAUNCHES}
 
 
 def exponential_method(Q, torch, stream, world, rank, dist, pk, jc_ref_mean, ntraj=20000):
@@ -798,7 +809,7 @@ def exponential_method(Q, torch, stream, world, rank, dist, pk, jc_ref_mean, ntr
     ref_traj = Q.qtm_traj_expect(ctx)
     ref_ms = Q.qtm_stats(ctx)["kernel_ms"]
     Q.qtm_destroy(ctx)
-    launches += 5
+    launches += RUN_LAUNCHES
     ex_traj = {}
     for key, prec in (("expo_df64", Q.QTM_PREC_DF64), ("expo_c64", Q.QTM_PREC_C64)):
         ctx = Q.qtm_create(dense, stream=int(stream.cuda_stream), precision=prec)
@@ -806,7 +817,7 @@ def exponential_method(Q, torch, stream, world, rank, dist, pk, jc_ref_mean, ntr
         Q.qtm_run_range(ctx, first, sample, dense.seed)
         ex_traj[key] = Q.qtm_traj_expect(ctx)
         Q.qtm_destroy(ctx)
-        launches += 5
+        launches += RUN_LAUNCHES
     nd = dense.dim
     dj = {"workload": "dense random open system (GUE H, N=256, 4 Ginibre C_n), 101 outputs on [0, 10], "
                       f"{world * count} trajectories", "unit": UNIT,
@@ -880,7 +891,7 @@ def learned_proposal(Q, torch, stream, world, rank, dist, ntraj=200000):
             "observable_error_vs_plain": float(np.abs(on["mean"] - off["mean"]).max()),
             "train": {"pairs": npairs, "steps": steps, "batch": 8192, "loss": loss, "loss_rate_estimate": base,
                       "collect_s": t1 - t0, "train_s": t2 - t1},
-            "launches": 5 + 3 * steps + 1 + 4 * 5}
+            "launches": RUN_LAUNCHES + 3 * steps + 1 + 4 * RUN_LAUNCHES}
 
 
 if __name__ == "__main__":

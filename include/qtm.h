@@ -173,19 +173,21 @@ typedef void *(*qtm_alloc_fn)(size_t bytes, void *stream, void *user);
 typedef void (*qtm_free_fn)(void *ptr, size_t bytes, void *stream, void *user);
 qtm_status qtm_set_allocator(qtm_alloc_fn alloc, qtm_free_fn free_fn, void *user);
 
-/* Validates and copies the problem, forms H_eff, uploads the operators to the
- * current CUDA device and returns a context bound to cuda_stream (a
- * cudaStream_t, may be NULL).  On error *out is NULL and the message is
- * available from qtm_last_error(NULL). */
+/* The problem statement of the paper's mpi_main (Sec. 3).  Validates and copies
+ * the problem, forms H_eff (Sec. 2.2, Eq. eqn:effective:hamiltonian), uploads the
+ * operators to the current CUDA device and returns a context bound to
+ * cuda_stream (a cudaStream_t, may be NULL).  On error *out is NULL and the
+ * message is available from qtm_last_error(NULL). */
 qtm_status qtm_create(const qtm_problem *problem, void *cuda_stream, qtm_ctx **out);
 
-/* Runs trajectories 0 .. ntraj-1 of the ensemble keyed by seed (asynchronous).
+/* Algorithm 1 (Sec. 2.2) for every trajectory: runs trajectories 0 .. ntraj-1 of
+ * the ensemble keyed by seed (asynchronous), then the ensemble sums of Sec. 3.
  * ntraj >= 0.  Replaces the results of any previous run of this context. */
 qtm_status qtm_run(qtm_ctx *ctx, int64_t ntraj, uint64_t seed);
 
 /* Same for global trajectory ids first .. first+ntraj-1 (first >= 0): a shard of a
- * larger ensemble, e.g. one GPU's share.  Results equal those of the same ids in
- * a single larger run. */
+ * larger ensemble, e.g. one GPU's share (the paper's worker processes, Sec. 3).
+ * Results equal those of the same ids in a single larger run. */
 qtm_status qtm_run_range(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64_t seed);
 
 /* Runs several ensembles at once: context i runs global trajectory ids
@@ -213,21 +215,73 @@ qtm_status qtm_autotune(qtm_ctx *ctx, int64_t sample, uint64_t seed, int32_t *gr
  * for any other pair.  Synchronises; discards the results of earlier runs. */
 qtm_status qtm_set_layout(qtm_ctx *ctx, int32_t group, int32_t rows);
 
-/* Ensemble mean (n_t * n_obs doubles, output-major: [j * n_obs + k]) and, if
- * stderr_out is not NULL, the standard error sqrt(var / n) with the sample
- * variance (n - 1 divisor; 0 when n < 2).  Synchronises; returns the first
- * per-trajectory failure of the run, if any. */
+/* The trajectory average of Sec. 3: ensemble mean (n_t * n_obs doubles,
+ * output-major: [j * n_obs + k]) and, if stderr_out is not NULL, the standard
+ * error sqrt(var / n) with the sample variance (n - 1 divisor; 0 when n < 2),
+ * computed from the run's exact moment words (below), so the result does not
+ * depend on how the trajectories were split over runs or GPUs.  NaN where a
+ * trajectory failed.  Synchronises; returns the first per-trajectory failure of
+ * the run, if any. */
 qtm_status qtm_expect(qtm_ctx *ctx, double *mean, double *stderr_out);
 
-/* Raw FP64 sums over the run's trajectories, for combining shards:
+/* Sums over the run's trajectories (from the same moment words):
  * sum[j * n_obs + k] = sum_i x_i, sumsq = sum_i x_i^2, *count = trajectories. */
 qtm_status qtm_sums(qtm_ctx *ctx, double *sum, double *sumsq, int64_t *count);
 
-/* Asynchronous device-side copy of the same sums into caller-owned DEVICE buffers
- * (n_t * n_obs doubles each), ordered on the context stream; for combining shards
- * with a collective (the averaging of Sec. 3 restated as one all-reduce) without
- * a host round trip. */
-qtm_status qtm_sums_device(qtm_ctx *ctx, double *sum_dev, double *sumsq_dev);
+/* ---------------------------------------------------------------------------
+ * Exact ensemble moments, for combining shards (the paper's two-level average of
+ * Sec. 3: each node averages its trajectories, the master averages the nodes).
+ * A value x of observable k is Re<psi|A_k|psi>/<psi|psi>, bounded in magnitude by
+ * max_i sum_j (|Re A_ij| + |Im A_ij|) < 2^(E_k - 1); E_k is the observable's scale
+ * exponent.  The library truncates x to an integer number of quanta 2^(E_k - 100)
+ * and x^2 (formed exactly) to quanta 2^(2 E_k - 100) and adds the integers, so the
+ * totals are exact: they do not depend on the order of addition or on how the
+ * trajectories were split, and the mean and standard error formed from them are
+ * the same bits for one run, for any set of shards, and for any order in which
+ * shards are combined (an integer all-reduce across GPUs included).  The
+ * truncation moves a value by less than 2^-99 of the bound.
+ *
+ * Moment words: QTM_MOMENT_WORDS int64 per output value j * n_obs + k, laid out
+ * [n_t * n_obs][QTM_MOMENT_WORDS]:
+ *   [0..2]  sum of the quanta of x   as d0 + d1 2^48 + d2 2^96
+ *   [3..5]  sum of the quanta of x^2 in the same digits
+ *   [6]     count of values that cannot be represented (NaN or Inf: a failed
+ *           trajectory); a non-zero count makes that output's mean and SE NaN.
+ * Word sets returned by the library have d0, d1 in [0, 2^48), so up to 16384 of
+ * them add word by word in int64 without overflow.
+ * ------------------------------------------------------------------------- */
+#define QTM_MOMENT_WORDS 7
+
+/* Moment words of the last run (HOST buffer of n_t * n_obs * QTM_MOMENT_WORDS),
+ * its trajectory count, and the n_obs scale exponents (may be NULL).  Synchronises. */
+qtm_status qtm_moments(qtm_ctx *ctx, int64_t *words, int64_t *count, int32_t *scale_exp);
+
+/* Asynchronous copy of the same words into a caller-owned DEVICE buffer, ordered
+ * on the context stream: the input of an integer sum all-reduce across GPUs (one
+ * shard per GPU), which is exact and therefore independent of the collective's
+ * reduction order. */
+qtm_status qtm_moments_device(qtm_ctx *ctx, int64_t *words_dev);
+
+/* Scale exponents E_k of the problem's n_obs observables (HOST output, n_obs
+ * int32); reads only dim, n_obs and A.  Needs no GPU. */
+qtm_status qtm_scale_exponents(const qtm_problem *problem, int32_t *scale_exp);
+
+/* Moment words of per-trajectory values held on the HOST, [ntraj][n_values] with
+ * n_values = n_t * n_obs (value p belongs to observable p % n_obs), by the same
+ * rule as a run: for shards computed elsewhere (or checking).  Needs no GPU. */
+qtm_status qtm_moments_of_values(const double *values, int64_t ntraj, int32_t n_values, int32_t n_obs,
+                                 const int32_t *scale_exp, int64_t *words);
+
+/* The master's average: adds the moment words of n_shards shards
+ * (words: HOST, [n_shards][n_values][QTM_MOMENT_WORDS], in rank order, although
+ * the integer sums make the order immaterial), counts[n_shards] trajectories each
+ * (total <= 2^40), and writes the ensemble mean and, where not NULL, the standard
+ * error (sample variance, n - 1 divisor), the sum and the sum of squares
+ * (HOST, n_values doubles each).  Equal, bit for bit, to qtm_expect / qtm_sums of
+ * one run over all the shards' trajectories.  Needs no GPU. */
+qtm_status qtm_combine_moments(int32_t n_shards, int32_t n_values, int32_t n_obs, const int32_t *scale_exp,
+                               const int64_t *words, const int64_t *counts, double *mean, double *stderr_out,
+                               double *sum, double *sumsq);
 
 /* Maximum scratch of qtm_ensemble_reduce_static, in doubles (4 MiB), and the
  * largest n_values it accepts. */
@@ -333,7 +387,8 @@ qtm_status qtm_proposal_enable(qtm_ctx *ctx, int32_t on, float margin);
 qtm_status qtm_mlp_loss_grad(const float *params, const float *x, const float *t, int64_t n, float *loss,
                              float *grad);
 
-/* Counters of the last run (synchronises). */
+/* Counters of the last run (synchronises): accepted and rejected steps of
+ * Algorithm 1 (B), products, jumps (C), root-find iterations. */
 qtm_status qtm_stats(qtm_ctx *ctx, qtm_stats_t *out);
 
 /* Human-readable message of the last error of ctx (or of the last failed

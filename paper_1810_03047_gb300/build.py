@@ -43,13 +43,19 @@ def _stamp() -> str:
                     + [os.path.join(ROOT, "include", "qtm.h"), __file__]):
         with open(f, "rb") as fh:
             h.update(f.encode() + fh.read())
-    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    h.update(" ".join(ARCH + NVCC_FLAGS + [f"{k}:{v}" for k, v in sorted(PER_FILE_FLAGS.items())]).encode())
     return h.hexdigest()
+
+
+# host files whose floating-point results must be the same bits on every host
+# architecture: no contraction of a multiply and an add into an FMA
+PER_FILE_FLAGS = {"moments.cpp": ["-Xcompiler", "-ffp-contract=off"]}
 
 
 def _compile(src: str, extra=()) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
-    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
+    cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *PER_FILE_FLAGS.get(os.path.basename(src), []), *extra, "-c", src,
+           "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {os.path.basename(src)}:\n{r.stdout}\n{r.stderr}")

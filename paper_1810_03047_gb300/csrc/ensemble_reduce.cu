@@ -9,6 +9,7 @@
 #include <mutex>
 
 #include "../../include/qtm.h"
+#include "moments.h"
 #include "qtm_launch.h"
 
 namespace qtm {
@@ -93,7 +94,63 @@ combine_devs(const double *__restrict__ pdev, int S, int P, long long ntraj, dou
     const double nt = (double)ntraj;
     se[p] = ntraj > 1 ? sqrt(d2 / (nt - 1.0) / nt) : 0.0;
 }
+// Exact moments (moments.h), pass 1: per segment and output value p, the moment
+// words of the segment's values, stored [segment][word][P] so that both passes
+// read and write along p.
+__global__ void __launch_bounds__(kThreads)
+segment_moments(const double *__restrict__ x, long long ntraj, int P, int n_obs, const int *__restrict__ scale_exp,
+                long long seg_len, long long *__restrict__ part)
+{
+    const int p = blockIdx.x * kThreads + threadIdx.x;
+    const long long s = blockIdx.y;
+    if (p >= P) return;
+    const int E = scale_exp[p % n_obs];
+    const double sc1 = pow2(kQuantBits - E), sc2 = pow2(kQuantBits - 2 * E), lim = pow2(E);
+    const long long b0 = s * seg_len;
+    const long long b1 = b0 + seg_len < ntraj ? b0 + seg_len : ntraj;
+    MomentAcc acc;
+    acc.clear();
+    for (long long b = b0; b < b1; ++b) acc.add(x[b * P + p], sc1, sc2, lim);
+    acc.normalize();
+    acc.store(part + s * kMomentWords * P + p, P);
+}
+
+// Pass 2: the segments' words added per output value (integers: any order gives
+// the same totals), normalised, stored [P][kMomentWords].
+__global__ void __launch_bounds__(kThreads)
+combine_moments(const long long *__restrict__ part, int S, int P, long long *__restrict__ words)
+{
+    const int p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= P) return;
+    long long w[kMomentWords] = {0, 0, 0, 0, 0, 0, 0};
+    for (int s = 0; s < S; ++s) {
+        const long long *q = part + (long long)s * kMomentWords * P + p;
+#pragma unroll
+        for (int k = 0; k < kMomentWords; ++k) w[k] += q[(long long)k * P];
+        if ((s & 1023) == 1023) {
+            normalize_digits(w);
+            normalize_digits(w + 3);
+        }
+    }
+    normalize_digits(w);
+    normalize_digits(w + 3);
+#pragma unroll
+    for (int k = 0; k < kMomentWords; ++k) words[(long long)p * kMomentWords + k] = w[k];
+}
 }  // namespace
+
+cudaError_t launch_ensemble_moments(const double *out, long long ntraj, int P, int n_obs, const int *scale_exp,
+                                    long long *partial, long long *words, cudaStream_t stream)
+{
+    if (P <= 0) return cudaSuccess;
+    const int S = reduce_segments(ntraj);
+    const long long seg = segment_length(ntraj);
+    const dim3 grid_seg((P + kThreads - 1) / kThreads, S);
+    const unsigned grid_p = (P + kThreads - 1) / kThreads;
+    segment_moments<<<grid_seg, kThreads, 0, stream>>>(out, ntraj, P, n_obs, scale_exp, seg, partial);
+    combine_moments<<<grid_p, kThreads, 0, stream>>>(partial, S, P, words);
+    return cudaGetLastError();
+}
 
 int reduce_segments(long long ntraj)
 {

@@ -21,6 +21,7 @@
 
 #include "../../include/qtm.h"
 #include "dense_tc.h"
+#include "moments.h"
 #include "proposal.cuh"
 #include "qtm_launch.h"
 
@@ -71,7 +72,8 @@ struct qtm_ctx {
     std::vector<Csr> Dops;       // -i H_k of the time-dependent terms
     std::vector<double> drive;   // 3 per term: a_k, omega_k, phi_k
     DevBuf d_ints, d_vals, d_t, d_psi0, d_queue, d_counters, d_first_error;
-    DevBuf d_out, d_partial, d_stats, d_njumps, d_jump_t, d_jump_ch;
+    DevBuf d_out, d_partial, d_moments, d_scale, d_njumps, d_jump_t, d_jump_ch;
+    std::vector<int> scale_exp;  // per observable: values are bounded by 2^(E - 1) (moments.h)
     // learned jump-time proposal
     DevBuf d_rec, d_mlp, d_X, d_T, d_gpart, d_lpart, d_grad, d_loss, d_m, d_v;
     int rec_stride = 0, rec_max = 0;
@@ -411,6 +413,21 @@ double op_norm_bound(const Csr &M)
     return std::max(rmax, cmax);
 }
 
+// Scale exponent of an observable's recorded values (moments.h): for Hermitian A,
+// |<psi|A|psi>| / <psi|psi> <= ||A||_2 <= max_i sum_j |A_ij| <= max_i sum_j
+// (|Re A_ij| + |Im A_ij|); the last form is summed with plain additions in CSR
+// order, so every host computes the same exponent.
+int observable_scale(const Csr &A)
+{
+    double bound = 0.0;
+    for (int i = 0; i < A.n; ++i) {
+        double r = 0.0;
+        for (int k = A.rp[i]; k < A.rp[i + 1]; ++k) r += std::fabs(A.val[k].real()) + std::fabs(A.val[k].imag());
+        bound = std::max(bound, r);
+    }
+    return qtm::scale_exponent(bound);
+}
+
 // X = sum_{m <= degree} (h M)^m / m! by Horner's rule, X <- I + (h/m) M X (dense row-major)
 void taylor_exp(const Csr &M, double h, int degree, cd *X)
 {
@@ -473,7 +490,7 @@ void destroy_ctx(qtm_ctx *ctx)
     cudaStreamSynchronize(ctx->stream);
     DevBuf *bufs[] = {&ctx->d_ints, &ctx->d_vals, &ctx->d_t, &ctx->d_psi0, &ctx->d_queue,
                       &ctx->d_counters, &ctx->d_first_error, &ctx->d_out, &ctx->d_partial,
-                      &ctx->d_stats, &ctx->d_njumps, &ctx->d_jump_t, &ctx->d_jump_ch,
+                      &ctx->d_moments, &ctx->d_scale, &ctx->d_njumps, &ctx->d_jump_t, &ctx->d_jump_ch,
                       &ctx->d_rec, &ctx->d_mlp, &ctx->d_X, &ctx->d_T, &ctx->d_gpart, &ctx->d_lpart,
                       &ctx->d_grad, &ctx->d_loss, &ctx->d_m, &ctx->d_v, &ctx->d_op, &ctx->d_state,
                       &ctx->d_col, &ctx->d_rhs, &ctx->d_dense, &ctx->d_expo};
@@ -751,6 +768,7 @@ qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
     ctx->M = effective_matrix(H, C);
     ctx->Cops = C;
     ctx->Aops = A;
+    for (int i = 0; i < p->n_obs; ++i) ctx->scale_exp.push_back(observable_scale(A[i]));
     // the tensor-core engine's control warps use one lane per row group of 32
     repack(ctx, p->precision == QTM_PREC_BF16X6 ? qtm::Layout{32, qtm::tc_padded_dim(n) / 32}
                                                 : qtm::layout_for_dim(n));
@@ -781,7 +799,7 @@ qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
     } allocs[] = {{&ctx->d_ints, ib}, {&ctx->d_vals, vb}, {&ctx->d_t, ctx->t.size() * sizeof(double)},
                   {&ctx->d_psi0, psi0_dev.size()}, {&ctx->d_queue, 16},
                   {&ctx->d_counters, qtm::kNumCounters * sizeof(unsigned long long)},
-                  {&ctx->d_first_error, 16}};
+                  {&ctx->d_first_error, 16}, {&ctx->d_scale, ctx->scale_exp.size() * sizeof(int)}};
     for (cudaEvent_t &ev : ctx->ev)
         if ((e = cudaEventCreate(&ev)) != cudaSuccess) {
             qtm_status s = cuda_fail(nullptr, e, "qtm_create: cudaEventCreate");
@@ -801,6 +819,9 @@ qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
                              cudaMemcpyHostToDevice, ctx->stream)) ||
         (e = cudaMemcpyAsync(ctx->d_psi0.p, psi0_dev.data(), psi0_dev.size(), cudaMemcpyHostToDevice,
                              ctx->stream)) ||
+        (!ctx->scale_exp.empty() &&
+         (e = cudaMemcpyAsync(ctx->d_scale.p, ctx->scale_exp.data(), ctx->scale_exp.size() * sizeof(int),
+                              cudaMemcpyHostToDevice, ctx->stream))) ||
         (e = cudaStreamSynchronize(ctx->stream))) {
         qtm_status s = cuda_fail(nullptr, e, "qtm_create: upload");
         destroy_ctx(ctx);
@@ -825,8 +846,8 @@ static qtm_status reserve_run(qtm_ctx *ctx, int64_t ntraj)
     const int S = qtm::reduce_segments(ntraj);
     cudaError_t e;
     if ((e = dev_reserve(ctx, ctx->d_out, (size_t)ntraj * P * sizeof(double))) ||
-        (e = dev_reserve(ctx, ctx->d_partial, 2 * (size_t)S * P * sizeof(double))) ||
-        (e = dev_reserve(ctx, ctx->d_stats, 4 * P * sizeof(double))))
+        (e = dev_reserve(ctx, ctx->d_partial, qtm::kMomentWords * (size_t)S * P * sizeof(long long))) ||
+        (e = dev_reserve(ctx, ctx->d_moments, qtm::kMomentWords * P * sizeof(long long))))
         return cuda_fail(ctx, e, "qtm_run: device allocation");
     if (ctx->precision == QTM_PREC_BF16X6 && ntraj > 0) {
         const size_t cols = (size_t)qtm::dense_tc_ctas(ntraj, ctx->sms) * qtm::kTcCols;
@@ -953,9 +974,9 @@ static qtm_status enqueue_run(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64
     }
     if (with_events && (e = cudaEventRecord(ctx->ev[1], s)) != cudaSuccess)
         return cuda_fail(ctx, e, "qtm_run: cudaEventRecord");
-    double *st = (double *)ctx->d_stats.p;
-    e = qtm::launch_ensemble_reduce((const double *)ctx->d_out.p, ntraj, (int)P, (double *)ctx->d_partial.p, st,
-                                    st + P, st + 2 * P, st + 3 * P, s);
+    e = qtm::launch_ensemble_moments((const double *)ctx->d_out.p, ntraj, (int)P, ctx->n_obs,
+                                     (const int *)ctx->d_scale.p, (long long *)ctx->d_partial.p,
+                                     (long long *)ctx->d_moments.p, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "qtm_run: ensemble reduction launch");
     if (with_events && (e = cudaEventRecord(ctx->ev[2], s)) != cudaSuccess)
         return cuda_fail(ctx, e, "qtm_run: cudaEventRecord");
@@ -1187,13 +1208,28 @@ static qtm_status sync_and_status(qtm_ctx *ctx)
     return QTM_OK;
 }
 
-static qtm_status copy_stats(qtm_ctx *ctx, int which, double *dst)
+// The run's moment words (host copy) and, from them, any of mean / standard
+// error / sum / sum of squares per output value (moments.h).
+static qtm_status copy_moments(qtm_ctx *ctx, std::vector<long long> &w)
 {
     const size_t P = (size_t)ctx->n_t * ctx->n_obs;
+    w.assign(P * qtm::kMomentWords, 0);
     if (P == 0) return QTM_OK;
-    cudaError_t e = cudaMemcpy(dst, (double *)ctx->d_stats.p + (size_t)which * P, P * sizeof(double),
-                               cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpy(w.data(), ctx->d_moments.p, w.size() * sizeof(long long), cudaMemcpyDeviceToHost);
     return e == cudaSuccess ? QTM_OK : cuda_fail(ctx, e, "cudaMemcpy");
+}
+
+static qtm_status finish_stats(qtm_ctx *ctx, double *mean, double *se, double *sum, double *sumsq)
+{
+    std::vector<long long> w;
+    qtm_status s = copy_moments(ctx, w);
+    if (s) return s;
+    const size_t P = (size_t)ctx->n_t * ctx->n_obs;
+    for (size_t p = 0; p < P; ++p)
+        qtm::moments_finish(w.data() + p * qtm::kMomentWords, ctx->last_ntraj, ctx->scale_exp[p % ctx->n_obs],
+                            mean ? mean + p : nullptr, se ? se + p : nullptr, sum ? sum + p : nullptr,
+                            sumsq ? sumsq + p : nullptr);
+    return QTM_OK;
 }
 
 qtm_status qtm_expect(qtm_ctx *ctx, double *mean, double *stderr_out)
@@ -1202,10 +1238,8 @@ qtm_status qtm_expect(qtm_ctx *ctx, double *mean, double *stderr_out)
     if (!mean) return fail(ctx, QTM_ERR_ARG, "qtm_expect: mean is NULL");
     qtm_status run_status = sync_and_status(ctx);
     if (run_status == QTM_ERR_STATE || run_status == QTM_ERR_CUDA) return run_status;
-    qtm_status s = copy_stats(ctx, 2, mean);
-    if (s) return s;
-    if (stderr_out && (s = copy_stats(ctx, 3, stderr_out))) return s;
-    return run_status;
+    qtm_status s = finish_stats(ctx, mean, stderr_out, nullptr, nullptr);
+    return s ? s : run_status;
 }
 
 qtm_status qtm_sums(qtm_ctx *ctx, double *sum, double *sumsq, int64_t *count)
@@ -1214,24 +1248,53 @@ qtm_status qtm_sums(qtm_ctx *ctx, double *sum, double *sumsq, int64_t *count)
     if (!sum || !sumsq || !count) return fail(ctx, QTM_ERR_ARG, "qtm_sums: NULL output");
     qtm_status run_status = sync_and_status(ctx);
     if (run_status == QTM_ERR_STATE || run_status == QTM_ERR_CUDA) return run_status;
-    qtm_status s;
-    if ((s = copy_stats(ctx, 0, sum)) || (s = copy_stats(ctx, 1, sumsq))) return s;
+    qtm_status s = finish_stats(ctx, nullptr, nullptr, sum, sumsq);
+    if (s) return s;
     *count = ctx->last_ntraj;
     return run_status;
 }
 
-qtm_status qtm_sums_device(qtm_ctx *ctx, double *sum_dev, double *sumsq_dev)
+qtm_status qtm_moments(qtm_ctx *ctx, int64_t *words, int64_t *count, int32_t *scale_exp)
 {
-    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_sums_device: ctx is NULL");
-    if (!sum_dev || !sumsq_dev) return fail(ctx, QTM_ERR_ARG, "qtm_sums_device: NULL output");
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_moments: ctx is NULL");
+    if (!words || !count) return fail(ctx, QTM_ERR_ARG, "qtm_moments: NULL output");
+    qtm_status run_status = sync_and_status(ctx);
+    if (run_status == QTM_ERR_STATE || run_status == QTM_ERR_CUDA) return run_status;
+    std::vector<long long> w;
+    qtm_status s = copy_moments(ctx, w);
+    if (s) return s;
+    std::memcpy(words, w.data(), w.size() * sizeof(long long));
+    *count = ctx->last_ntraj;
+    if (scale_exp)
+        for (int k = 0; k < ctx->n_obs; ++k) scale_exp[k] = ctx->scale_exp[k];
+    return run_status;
+}
+
+qtm_status qtm_moments_device(qtm_ctx *ctx, int64_t *words_dev)
+{
+    if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_moments_device: ctx is NULL");
+    if (!words_dev) return fail(ctx, QTM_ERR_ARG, "qtm_moments_device: NULL output");
     if (ctx->last_ntraj < 0) return fail(ctx, QTM_ERR_STATE, "no qtm_run on this context yet");
     const size_t P = (size_t)ctx->n_t * ctx->n_obs;
     if (P == 0) return QTM_OK;
-    const double *st = (const double *)ctx->d_stats.p;
-    cudaError_t e;
-    if ((e = cudaMemcpyAsync(sum_dev, st, P * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream)) ||
-        (e = cudaMemcpyAsync(sumsq_dev, st + P, P * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream)))
-        return cuda_fail(ctx, e, "qtm_sums_device: cudaMemcpyAsync");
+    cudaError_t e = cudaMemcpyAsync(words_dev, ctx->d_moments.p, P * qtm::kMomentWords * sizeof(long long),
+                                    cudaMemcpyDeviceToDevice, ctx->stream);
+    return e == cudaSuccess ? QTM_OK : cuda_fail(ctx, e, "qtm_moments_device: cudaMemcpyAsync");
+}
+
+qtm_status qtm_scale_exponents(const qtm_problem *p, int32_t *scale_exp)
+{
+    if (!p || !scale_exp) return fail(nullptr, QTM_ERR_ARG, "qtm_scale_exponents: NULL argument");
+    if (p->dim < 1 || p->n_obs < 0 || (p->n_obs > 0 && !p->A))
+        return fail(nullptr, QTM_ERR_ARG, "qtm_scale_exponents: need dim >= 1 and the n_obs observables");
+    char buf[32];
+    for (int i = 0; i < p->n_obs; ++i) {
+        std::snprintf(buf, sizeof buf, "A[%d]", i);
+        Csr A;
+        qtm_status st = read_op(p->A[i], p->dim, buf, A);
+        if (st) return st;
+        scale_exp[i] = observable_scale(A);
+    }
     return QTM_OK;
 }
 

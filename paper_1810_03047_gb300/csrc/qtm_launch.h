@@ -162,6 +162,12 @@ cudaError_t launch_ensemble_reduce(const double *out, long long ntraj, int P, do
                                    double *sum, double *sumsq, double *mean, double *se,
                                    cudaStream_t stream);
 
+// Exact ensemble moments (moments.h) of out[ntraj][P], P = n_t * n_obs, with the
+// per-observable scale exponents scale_exp[n_obs] (device): words[P][kMomentWords].
+// partial must hold kMomentWords * S * P int64 for S = reduce_segments(ntraj).
+cudaError_t launch_ensemble_moments(const double *out, long long ntraj, int P, int n_obs, const int *scale_exp,
+                                    long long *partial, long long *words, cudaStream_t stream);
+
 // Sets the message returned by qtm_last_error(NULL).
 void set_last_error(const char *msg);
 

@@ -42,7 +42,8 @@ QTM_METHOD_EXPONENTIAL = 1
 
 # every entry point declared in include/qtm.h
 EXPORTS = ["qtm_set_allocator", "qtm_create", "qtm_run", "qtm_run_range", "qtm_expect", "qtm_sums",
-           "qtm_sums_device",
+           "qtm_moments", "qtm_moments_device", "qtm_scale_exponents", "qtm_moments_of_values",
+           "qtm_combine_moments",
            "qtm_traj_expect", "qtm_jumps", "qtm_stats", "qtm_last_error", "qtm_status_string",
            "qtm_destroy", "qtm_version", "qtm_ensemble_reduce_static", "qtm_run_batch", "qtm_autotune",
            "qtm_set_layout", "qtm_proposal_collect", "qtm_proposal_pairs", "qtm_proposal_train",
@@ -51,6 +52,7 @@ EXPORTS = ["qtm_set_allocator", "qtm_create", "qtm_run", "qtm_run_range", "qtm_e
            "qtm_propagator"]
 
 QTM_PROPOSAL_FLOATS = 4685
+QTM_MOMENT_WORDS = 7
 MLP_PARAMS = 4673
 
 
@@ -103,7 +105,16 @@ def lib():
             L.qtm_expect.argtypes = [ct.c_void_p, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
             L.qtm_sums.argtypes = [ct.c_void_p, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double),
                                    ct.POINTER(ct.c_int64)]
-            L.qtm_sums_device.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p]
+            i64p = ct.POINTER(ct.c_int64)
+            i32p = ct.POINTER(ct.c_int32)
+            L.qtm_moments.argtypes = [ct.c_void_p, i64p, i64p, i32p]
+            L.qtm_moments_device.argtypes = [ct.c_void_p, ct.c_void_p]
+            L.qtm_scale_exponents.argtypes = [ct.POINTER(QtmProblem), i32p]
+            L.qtm_moments_of_values.argtypes = [ct.POINTER(ct.c_double), ct.c_int64, ct.c_int32, ct.c_int32, i32p,
+                                                i64p]
+            L.qtm_combine_moments.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, i32p, i64p, i64p,
+                                              ct.POINTER(ct.c_double), ct.POINTER(ct.c_double),
+                                              ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
             L.qtm_traj_expect.argtypes = [ct.c_void_p, ct.POINTER(ct.c_double)]
             L.qtm_jumps.argtypes = [ct.c_void_p, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_double),
                                     ct.POINTER(ct.c_int32)]
@@ -152,7 +163,9 @@ def lib():
             for name in ("qtm_proposal_collect", "qtm_proposal_pairs", "qtm_proposal_train", "qtm_proposal_set",
                          "qtm_proposal_get", "qtm_proposal_enable", "qtm_mlp_loss_grad"):
                 getattr(L, name).restype = ct.c_int
-            for name in ("qtm_create", "qtm_run", "qtm_run_range", "qtm_expect", "qtm_sums", "qtm_sums_device",
+            for name in ("qtm_create", "qtm_run", "qtm_run_range", "qtm_expect", "qtm_sums", "qtm_moments",
+                         "qtm_moments_device", "qtm_scale_exponents", "qtm_moments_of_values",
+                         "qtm_combine_moments",
                          "qtm_traj_expect", "qtm_jumps", "qtm_stats", "qtm_set_allocator"):
                 getattr(L, name).restype = ct.c_int
             _lib = L
@@ -411,9 +424,60 @@ def qtm_sums(ctx: Ctx):
     return s, s2, n.value
 
 
-def qtm_sums_device(ctx: Ctx, sum_dev_ptr: int, sumsq_dev_ptr: int):
-    """Asynchronous copy of the run's FP64 sums into caller-owned device buffers."""
-    _check(lib().qtm_sums_device(ctx.handle, ct.c_void_p(sum_dev_ptr), ct.c_void_p(sumsq_dev_ptr)), ctx)
+def _i64p(a):
+    return a.ctypes.data_as(ct.POINTER(ct.c_int64))
+
+
+def _i32p(a):
+    return a.ctypes.data_as(ct.POINTER(ct.c_int32))
+
+
+def qtm_moments(ctx: Ctx):
+    """(words [n_t * n_obs, QTM_MOMENT_WORDS] int64, trajectory count, scale exponents [n_obs])."""
+    w = np.zeros((ctx.n_t * ctx.n_obs, QTM_MOMENT_WORDS), np.int64)
+    n = ct.c_int64()
+    e = np.zeros(max(1, ctx.n_obs), np.int32)
+    _check(lib().qtm_moments(ctx.handle, _i64p(w), ct.byref(n), _i32p(e)), ctx)
+    return w, n.value, e[:ctx.n_obs]
+
+
+def qtm_moments_device(ctx: Ctx, words_dev_ptr: int):
+    """Asynchronous copy of the run's moment words into a caller-owned device buffer."""
+    _check(lib().qtm_moments_device(ctx.handle, ct.c_void_p(words_dev_ptr)), ctx)
+
+
+def qtm_scale_exponents(prob) -> np.ndarray:
+    """Scale exponents of the problem's observables (host only, no GPU)."""
+    p, keep = make_problem(prob)
+    e = np.zeros(max(1, len(prob.A)), np.int32)
+    _check(lib().qtm_scale_exponents(ct.byref(p), _i32p(e)))
+    return e[:len(prob.A)]
+
+
+def qtm_moments_of_values(values, n_obs: int, scale_exp) -> np.ndarray:
+    """Moment words of host values [ntraj, n_t, n_obs] (or [ntraj, n_t * n_obs]); no GPU."""
+    v = np.ascontiguousarray(values, dtype=np.float64)
+    ntraj = v.shape[0]
+    P = int(np.prod(v.shape[1:])) if v.ndim > 1 else 0
+    e = np.ascontiguousarray(scale_exp, dtype=np.int32)
+    w = np.zeros((P, QTM_MOMENT_WORDS), np.int64)
+    _check(lib().qtm_moments_of_values(_dp(v), int(ntraj), int(P), int(n_obs), _i32p(e), _i64p(w)))
+    return w
+
+
+def qtm_combine_moments(words, counts, n_obs: int, scale_exp):
+    """(mean, stderr, sum, sumsq), each [n_values], of shards' moment words
+    [n_shards, n_values, QTM_MOMENT_WORDS] with counts [n_shards]; no GPU."""
+    w = np.ascontiguousarray(words, dtype=np.int64)
+    if w.ndim == 2:
+        w = w[None]
+    c = np.ascontiguousarray(np.atleast_1d(counts), dtype=np.int64)
+    e = np.ascontiguousarray(scale_exp, dtype=np.int32)
+    P = w.shape[1]
+    out = [np.zeros(P) for _ in range(4)]
+    _check(lib().qtm_combine_moments(int(w.shape[0]), int(P), int(n_obs), _i32p(e), _i64p(w), _i64p(c),
+                                     *[_dp(o) for o in out]))
+    return tuple(out)
 
 
 def qtm_traj_expect(ctx: Ctx, check: bool = True):
