@@ -81,7 +81,8 @@ def parse():
                     help="skip the exponential-method legs (stiff Purcell system, Jaynes-Cummings)")
     ap.add_argument("--no-ising", action="store_true",
                     help="skip the batched Ising-chain measurement (L = 6..10 in one CUDA graph)")
-    ap.add_argument("--only", choices=["c128", "df64", "c64", "dense", "expo_purcell", "expo_jc", "expo_dense"], default=None,
+    ap.add_argument("--only", choices=["c128", "df64", "c64", "dense", "expo_purcell", "expo_jc", "expo_dense", "peak"],
+                    default=None,
                     help="time one arithmetic only (profiling); no observable-error comparison.  'dense': the "
                          "tensor-core engine on the dense N = 256 system with --ntraj trajectories")
     ap.add_argument("--dense-t-end", type=float, default=10.0, help="--only dense: end of the time grid")
@@ -268,15 +269,54 @@ FP32_LANES_PER_SM = 128
 DF_INSTR_PER_FLOP = 6
 
 
-def peaks():
+def nominal_peaks():
+    """Peaks from the unit counts and the maximum SM clock (context for the measured ones)."""
     fp64 = SMS * FP64_FMA_PER_SM_CLK * 2 * SM_MAX_MHZ * 1e6 / 1e12
     fp32_instr = SMS * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6
-    return {"c128": (fp64, "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2070 MHz (GB300 nominal 1.25 TFLOP/s)"),
-            "df64": (fp32_instr / DF_INSTR_PER_FLOP / 1e12,
-                     "FP64-class flops on the FP32 pipe: 152 SMs x 128 FP32 lanes x 2070 MHz = 40.3e12 "
-                     "instr/s, 12 instructions per double-float multiply-add (2 flop)"),
-            "c64": (2 * fp32_instr / 1e12, "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz"),
-            "hbm": _hbm_peak()}
+    return {"c128": fp64, "df64": fp32_instr / DF_INSTR_PER_FLOP / 1e12, "c64": 2 * fp32_instr / 1e12}
+
+
+def peaks(measured=None):
+    """Roofline denominators: the arithmetic peaks measured in this run (probe
+    kernels, of measured), falling back to the nominal unit-count figures."""
+    nom = nominal_peaks()
+    m = measured or {}
+    out = {}
+    for key, probe, what in (("c128", "fp64", "FP64 FMA chains"), ("c64", "fp32", "FP32 FMA chains"),
+                             ("df64", "df64", "double-float multiply-add chains (12 FP32 instructions, 2 FP64-class "
+                                              "flop each)")):
+        if m.get(probe):
+            out[key] = (m[probe], f"measured in this run by the probe kernel ({what} on every SM, CUDA events), "
+                                  f"of measured; nominal {nom[key]:.3g} TFLOP/s from unit counts at 2070 MHz")
+        else:
+            out[key] = (nom[key], f"nominal from unit counts at 2070 MHz ({what}), no measurement")
+    out["hbm"] = _hbm_peak()
+    return out
+
+
+def measured_arith_peaks(Q, torch, stream, seconds=1.0):
+    """The arithmetic peaks of this GPU, measured in this run by the library's probe
+    kernels (independent multiply-add chains on every SM; qtm_arith_peak_launch),
+    timed with CUDA events on `stream`: each probe is calibrated on a short launch,
+    then run for about `seconds`, best of three.  TFLOP/s per kind."""
+    scratch = torch.zeros(4, dtype=torch.float64, device="cuda")
+    out = {}
+    for name, kind in (("fp64", Q.QTM_PEAK_FP64), ("fp32", Q.QTM_PEAK_FP32), ("df64", Q.QTM_PEAK_DF64)):
+        iters, best = 1000, 0.0
+        for rep in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            flop = Q.qtm_arith_peak_launch(kind, iters, scratch.data_ptr(), int(stream.cuda_stream))
+            e1.record(stream)
+            e1.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            if rep >= 2:
+                best = max(best, flop / sec / 1e12)
+            else:  # calibration launches
+                iters = max(1000, int(iters * seconds / max(sec, 1e-6)))
+        out[name] = best
+    return out
 
 
 def _hbm_peak():
@@ -315,7 +355,8 @@ def main():
     words = torch.zeros((P, Q.QTM_MOMENT_WORDS), dtype=torch.int64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
     F = flops_per_attempt(prob.dim, nnz_m)
-    pk = peaks()
+    arith = measured_arith_peaks(Q, torch, stream)
+    pk = peaks(arith)
     codes = {"c128": Q.QTM_PREC_C128, "df64": Q.QTM_PREC_DF64, "c64": Q.QTM_PREC_C64}
 
     def timed(prec_name, steps, warmup):
@@ -382,6 +423,17 @@ def main():
 
     clocks = ClockSampler(local)
     clocks.start()
+    if args.only == "peak":
+        clk = clocks.stop()
+        if rank == 0:
+            nom = nominal_peaks()
+            print(json.dumps({"metric": "arithmetic peaks (probe kernels)", "unit": "TFLOP/s",
+                              "fp64": arith["fp64"], "fp32": arith["fp32"], "df64": arith["df64"],
+                              "nominal": {"fp64": nom["c128"], "fp32": nom["c64"], "df64": nom["df64"]},
+                              "gpu_launches": 15, "clocks": clk}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
     if args.only == "dense":
         from paper_1810_03047_gb300 import systems as S
         dprob = S.dense_random(ntraj=args.ntraj, t_end=args.dense_t_end, n_t=args.dense_outputs)
@@ -506,8 +558,10 @@ def main():
         "roofline": head["roofline"],
         "e2e": {"value": world * ntraj * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": ref["launches"] + fast["launches"] + mixed["launches"],
+        "gpu_launches": ref["launches"] + fast["launches"] + mixed["launches"] + 15,  # + the peak probes
         "clocks": clk,
+        "arithmetic_peaks_tflops": dict(arith, note="measured in this run by the probe kernels "
+                                                     "(qtm_arith_peak_launch), best of three ~1 s launches"),
     }
     if not args.no_ising:
         line["ising_batch"] = ising_batch(Q, torch, stream, world, rank, dist)

@@ -477,6 +477,26 @@ qtm_status qtm_expo_ladder(const qtm_ctx *ctx, int32_t *levels, double *delta);
  * from qtm_last_error(NULL). */
 qtm_status qtm_propagator(const qtm_problem *problem, double dt, double *out);
 
+/* ---------------------------------------------------------------------------
+ * Arithmetic peaks of the current GPU, for the roofline fractions of the
+ * trajectory kernels (whose state never leaves the SM, so arithmetic bounds
+ * them).  The paper has no counterpart: this measures the machine.
+ * ------------------------------------------------------------------------- */
+enum {
+    QTM_PEAK_FP64 = 0,  /* FP64 fused multiply-adds (the complex128 path's pipe) */
+    QTM_PEAK_FP32 = 1,  /* FP32 fused multiply-adds (the complex64 path's pipe) */
+    QTM_PEAK_DF64 = 2   /* double-float multiply-adds as the double-float path forms them
+                           (12 FP32 instructions each), counted as two FP64-class flops */
+};
+
+/* Launches (asynchronously, on cuda_stream) one probe kernel of `kind`: a grid
+ * that fills every SM, each thread running 8 independent multiply-add chains of
+ * `iters` steps (>= 1).  scratch_dev: a DEVICE buffer of at least 8 bytes (never
+ * written in practice; it keeps the chains from being optimised away).  *flop =
+ * the launch's flops (2 per multiply-add); the caller times the launch with
+ * events on the same stream. */
+qtm_status qtm_arith_peak_launch(int32_t kind, int64_t iters, void *scratch_dev, void *cuda_stream, double *flop);
+
 /* Releases the context's device memory (after synchronising its stream). NULL is ignored. */
 void qtm_destroy(qtm_ctx *ctx);
 

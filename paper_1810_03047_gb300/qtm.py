@@ -43,7 +43,7 @@ QTM_METHOD_EXPONENTIAL = 1
 # every entry point declared in include/qtm.h
 EXPORTS = ["qtm_set_allocator", "qtm_create", "qtm_run", "qtm_run_range", "qtm_expect", "qtm_sums",
            "qtm_moments", "qtm_moments_device", "qtm_scale_exponents", "qtm_moments_of_values",
-           "qtm_combine_moments",
+           "qtm_combine_moments", "qtm_arith_peak_launch",
            "qtm_traj_expect", "qtm_jumps", "qtm_stats", "qtm_last_error", "qtm_status_string",
            "qtm_destroy", "qtm_version", "qtm_ensemble_reduce_static", "qtm_run_batch", "qtm_autotune",
            "qtm_set_layout", "qtm_proposal_collect", "qtm_proposal_pairs", "qtm_proposal_train",
@@ -53,6 +53,9 @@ EXPORTS = ["qtm_set_allocator", "qtm_create", "qtm_run", "qtm_run_range", "qtm_e
 
 QTM_PROPOSAL_FLOATS = 4685
 QTM_MOMENT_WORDS = 7
+QTM_PEAK_FP64 = 0
+QTM_PEAK_FP32 = 1
+QTM_PEAK_DF64 = 2
 MLP_PARAMS = 4673
 
 
@@ -108,6 +111,8 @@ def lib():
             i64p = ct.POINTER(ct.c_int64)
             i32p = ct.POINTER(ct.c_int32)
             L.qtm_moments.argtypes = [ct.c_void_p, i64p, i64p, i32p]
+            L.qtm_arith_peak_launch.argtypes = [ct.c_int32, ct.c_int64, ct.c_void_p, ct.c_void_p,
+                                                ct.POINTER(ct.c_double)]
             L.qtm_moments_device.argtypes = [ct.c_void_p, ct.c_void_p]
             L.qtm_scale_exponents.argtypes = [ct.POINTER(QtmProblem), i32p]
             L.qtm_moments_of_values.argtypes = [ct.POINTER(ct.c_double), ct.c_int64, ct.c_int32, ct.c_int32, i32p,
@@ -165,7 +170,7 @@ def lib():
                 getattr(L, name).restype = ct.c_int
             for name in ("qtm_create", "qtm_run", "qtm_run_range", "qtm_expect", "qtm_sums", "qtm_moments",
                          "qtm_moments_device", "qtm_scale_exponents", "qtm_moments_of_values",
-                         "qtm_combine_moments",
+                         "qtm_combine_moments", "qtm_arith_peak_launch",
                          "qtm_traj_expect", "qtm_jumps", "qtm_stats", "qtm_set_allocator"):
                 getattr(L, name).restype = ct.c_int
             _lib = L
@@ -439,6 +444,14 @@ def qtm_moments(ctx: Ctx):
     e = np.zeros(max(1, ctx.n_obs), np.int32)
     _check(lib().qtm_moments(ctx.handle, _i64p(w), ct.byref(n), _i32p(e)), ctx)
     return w, n.value, e[:ctx.n_obs]
+
+
+def qtm_arith_peak_launch(kind: int, iters: int, scratch_dev_ptr: int, stream: int = 0) -> float:
+    """Launches one arithmetic-peak probe kernel on `stream`; returns its flop count."""
+    f = ct.c_double()
+    _check(lib().qtm_arith_peak_launch(int(kind), int(iters), ct.c_void_p(scratch_dev_ptr), ct.c_void_p(stream or 0),
+                                       ct.byref(f)))
+    return f.value
 
 
 def qtm_moments_device(ctx: Ctx, words_dev_ptr: int):
