@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-peak-probe", action="store_true",
+                    help="skip the arithmetic-peak probes (profiling runs): roofline against the nominal peaks")
     ap.add_argument("--no-paper", action="store_true",
                     help="skip the paper's own examples (Sec. 4.1 unitary, Sec. 4.2 trilinear OPA)")
     ap.add_argument("--no-dense", action="store_true",
@@ -355,7 +357,7 @@ def main():
     words = torch.zeros((P, Q.QTM_MOMENT_WORDS), dtype=torch.int64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
     F = flops_per_attempt(prob.dim, nnz_m)
-    arith = measured_arith_peaks(Q, torch, stream)
+    arith = {} if args.no_peak_probe else measured_arith_peaks(Q, torch, stream)
     pk = peaks(arith)
     codes = {"c128": Q.QTM_PREC_C128, "df64": Q.QTM_PREC_DF64, "c64": Q.QTM_PREC_C64}
 
@@ -428,7 +430,7 @@ def main():
         if rank == 0:
             nom = nominal_peaks()
             print(json.dumps({"metric": "arithmetic peaks (probe kernels)", "unit": "TFLOP/s",
-                              "fp64": arith["fp64"], "fp32": arith["fp32"], "df64": arith["df64"],
+                              "fp64": arith.get("fp64"), "fp32": arith.get("fp32"), "df64": arith.get("df64"),
                               "nominal": {"fp64": nom["c128"], "fp32": nom["c64"], "df64": nom["df64"]},
                               "gpu_launches": 15, "clocks": clk}), flush=True)
         if world > 1:
@@ -558,13 +560,13 @@ def main():
         "roofline": head["roofline"],
         "e2e": {"value": world * ntraj * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": ref["launches"] + fast["launches"] + mixed["launches"] + 15,  # + the peak probes
+        "gpu_launches": ref["launches"] + fast["launches"] + mixed["launches"] + (15 if arith else 0),
         "clocks": clk,
         "arithmetic_peaks_tflops": dict(arith, note="measured in this run by the probe kernels "
                                                      "(qtm_arith_peak_launch), best of three ~1 s launches"),
     }
     if not args.no_ising:
-        line["ising_batch"] = ising_batch(Q, torch, stream, world, rank, dist)
+        line["ising_batch"] = ising_batch(Q, torch, stream, world, rank, dist, pk)
         line["gpu_launches"] += line["ising_batch"].pop("launches")
     if not args.no_paper:
         line["paper_workloads"] = paper_workloads(Q, torch, stream, world, rank, dist)
@@ -587,12 +589,15 @@ def main():
     return 0
 
 
-def ising_batch(Q, torch, stream, world, rank, dist):
+def ising_batch(Q, torch, stream, world, rank, dist, pk):
     """The uneven batched ensemble: open transverse-field Ising chains L = 6..10
     (N = 64..1024, 2L channels) with 50k/20k/10k/5k/2k trajectories (seed 7), all
     five systems in one CUDA-graph launch.  Double-float with autotuned lane
     layouts is timed (1 warm-up, 1 timed pass) and compared with the complex128
-    batch on the same trajectories."""
+    batch on the same trajectories.  Roofline: algorithmic flops of every attempt
+    of every system (6 * 8 nnz(M) + 26 * 4 N, nnz(M) = (L + 1) N) over the batch
+    time, against the measured double-float peak; and the same for the L = 10
+    kernel timed alone."""
     from paper_1810_03047_gb300 import shards
     from paper_1810_03047_gb300 import systems as S
     Ls = [6, 7, 8, 9, 10]
@@ -619,16 +624,34 @@ def ising_batch(Q, torch, stream, world, rank, dist):
         ref_ms.append(e0.elapsed_time(e1))
     ms = ref_ms[-1]
     err = max(float(np.abs(Q.qtm_expect(c)[0] - m).max()) for c, m in zip(fast, ref_means))
+    flop = 0.0
+    for c, p in zip(fast, probs):
+        st = Q.qtm_stats(c)
+        flop += flops_per_attempt(p.dim, _nnz_effective(p)) * (st["accepted"] + st["rejected"])
+    peak, note = pk["df64"]
+    achieved = flop / (ms / 1e3) / 1e12
+    # the L = 10 kernel alone (the largest share of the batch's device time)
+    c10, p10 = fast[-1], probs[-1]
+    Q.qtm_run_range(c10, firsts[-1], counts[-1], 7)
+    st10 = Q.qtm_stats(c10)
+    a10 = flops_per_attempt(p10.dim, _nnz_effective(p10)) * (st10["accepted"] + st10["rejected"]) \
+        / (st10["kernel_ms"] / 1e3) / 1e12
     t = torch.tensor([ms], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     for c in ref + fast:
         Q.qtm_destroy(c)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "qtm::mcwf_kernel<df64, autotuned layouts> x 5 systems in one graph",
+            "peak_note": note,
+            "l10_alone": {"kernel": f"qtm::mcwf_kernel<df64,{st10['kernel_group']},{st10['kernel_rows']}>",
+                          "kernel_ms": st10["kernel_ms"], "achieved": a10, "frac": a10 / peak}}
     return {"workload": "transverse-field Ising chains L=6..10 (N=64..1024, J=1, h=0.7, decay 0.05 and "
                         "dephasing 0.02 per site), 50k/20k/10k/5k/2k trajectories, 201 outputs on [0,20], "
                         "one CUDA-graph launch", "precision": "df64",
             "value": world * sum(counts) / (float(t.item()) / 1e3), "unit": UNIT, "ms_per_step": float(t.item()),
-            "observable_error": err, "layouts": [list(x) for x in layouts], "launches": 2 * 5 * RUN_LAUNCHES}
+            "observable_error": err, "layouts": [list(x) for x in layouts], "roofline": roof,
+            "launches": 2 * 5 * RUN_LAUNCHES + RUN_LAUNCHES}
 
 
 def paper_workloads(Q, torch, stream, world, rank, dist):

@@ -233,24 +233,24 @@ qtm_status qtm_sums(qtm_ctx *ctx, double *sum, double *sumsq, int64_t *count);
  * Sec. 3: each node averages its trajectories, the master averages the nodes).
  * A value x of observable k is Re<psi|A_k|psi>/<psi|psi>, bounded in magnitude by
  * max_i sum_j (|Re A_ij| + |Im A_ij|) < 2^(E_k - 1); E_k is the observable's scale
- * exponent.  The library truncates x to an integer number of quanta 2^(E_k - 100)
- * and x^2 (formed exactly) to quanta 2^(2 E_k - 100) and adds the integers, so the
- * totals are exact: they do not depend on the order of addition or on how the
- * trajectories were split, and the mean and standard error formed from them are
- * the same bits for one run, for any set of shards, and for any order in which
- * shards are combined (an integer all-reduce across GPUs included).  The
- * truncation moves a value by less than 2^-99 of the bound.
+ * exponent.  The library truncates x to an integer q(x) of quanta 2^(E_k - 100)
+ * and adds q(x) and q(x)^2 as integers, so the totals are exact: they do not
+ * depend on the order of addition or on how the trajectories were split, and the
+ * mean and standard error formed from them (the variance of the quantised values,
+ * exactly) are the same bits for one run, for any set of shards, and for any
+ * order in which shards are combined (an integer all-reduce across GPUs
+ * included).  The truncation moves a value by less than 2^-99 of the bound.
  *
  * Moment words: QTM_MOMENT_WORDS int64 per output value j * n_obs + k, laid out
  * [n_t * n_obs][QTM_MOMENT_WORDS]:
- *   [0..2]  sum of the quanta of x   as d0 + d1 2^48 + d2 2^96
- *   [3..5]  sum of the quanta of x^2 in the same digits
- *   [6]     count of values that cannot be represented (NaN or Inf: a failed
+ *   [0..2]  sum of q(x)   as d0 + d1 2^48 + d2 2^96
+ *   [3..7]  sum of q(x)^2 as d0 + d1 2^48 + ... + d4 2^192
+ *   [8]     count of values that cannot be represented (NaN or Inf: a failed
  *           trajectory); a non-zero count makes that output's mean and SE NaN.
- * Word sets returned by the library have d0, d1 in [0, 2^48), so up to 16384 of
- * them add word by word in int64 without overflow.
+ * Word sets returned by the library have every digit but the last of each sum in
+ * [0, 2^48), so up to 16384 of them add word by word in int64 without overflow.
  * ------------------------------------------------------------------------- */
-#define QTM_MOMENT_WORDS 7
+#define QTM_MOMENT_WORDS 9
 
 /* Moment words of the last run (HOST buffer of n_t * n_obs * QTM_MOMENT_WORDS),
  * its trajectory count, and the n_obs scale exponents (may be NULL).  Synchronises. */
@@ -314,10 +314,12 @@ qtm_status qtm_combine_moments(int32_t n_shards, int32_t n_values, int32_t n_obs
  * overlaps on the GPU (different streams without ordering between them) race
  * on it and give wrong results; order them on one stream.  Each call writes
  * every scratch element it reads before reading it, so nothing needs clearing
- * between calls.  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress, with that device current), so make that first
- * call before any stream capture on that device.  The call is asynchronous;
- * results are ready when the stream reaches it. */
+ * between calls.  The first call in each CUDA context -- on each device, and
+ * again once a device's context has been destroyed and created anew (after
+ * cudaDeviceReset, say) -- looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it for that
+ * context, so make that first call before any stream capture on that device.
+ * The call is asynchronous; results are ready when the stream reaches it. */
 qtm_status qtm_ensemble_reduce_static(const double *values_dev, int64_t ntraj, int32_t n_values,
                                       double *sum_dev, double *sumsq_dev, double *mean_dev,
                                       double *stderr_dev, void *cuda_stream);

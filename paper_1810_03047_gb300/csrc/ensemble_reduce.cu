@@ -105,12 +105,12 @@ segment_moments(const double *__restrict__ x, long long ntraj, int P, int n_obs,
     const long long s = blockIdx.y;
     if (p >= P) return;
     const int E = scale_exp[p % n_obs];
-    const double sc1 = pow2(kQuantBits - E), sc2 = pow2(kQuantBits - 2 * E), lim = pow2(E);
+    const double sc = pow2(kQuantBits - E), lim = pow2(E);
     const long long b0 = s * seg_len;
     const long long b1 = b0 + seg_len < ntraj ? b0 + seg_len : ntraj;
     MomentAcc acc;
     acc.clear();
-    for (long long b = b0; b < b1; ++b) acc.add(x[b * P + p], sc1, sc2, lim);
+    for (long long b = b0; b < b1; ++b) acc.add(x[b * P + p], sc, lim);
     acc.normalize();
     acc.store(part + s * kMomentWords * P + p, P);
 }
@@ -122,18 +122,18 @@ combine_moments(const long long *__restrict__ part, int S, int P, long long *__r
 {
     const int p = blockIdx.x * kThreads + threadIdx.x;
     if (p >= P) return;
-    long long w[kMomentWords] = {0, 0, 0, 0, 0, 0, 0};
+    long long w[kMomentWords] = {};
     for (int s = 0; s < S; ++s) {
         const long long *q = part + (long long)s * kMomentWords * P + p;
 #pragma unroll
         for (int k = 0; k < kMomentWords; ++k) w[k] += q[(long long)k * P];
         if ((s & 1023) == 1023) {
-            normalize_digits(w);
-            normalize_digits(w + 3);
+            normalize_digits(w + kS1, kS1Digits);
+            normalize_digits(w + kS2, kS2Digits);
         }
     }
-    normalize_digits(w);
-    normalize_digits(w + 3);
+    normalize_digits(w + kS1, kS1Digits);
+    normalize_digits(w + kS2, kS2Digits);
 #pragma unroll
     for (int k = 0; k < kMomentWords; ++k) words[(long long)p * kMomentWords + k] = w[k];
 }
@@ -187,26 +187,58 @@ namespace {
 
 static __device__ __align__(256) double g_static_scratch[QTM_STATIC_SCRATCH_DOUBLES];
 
-constexpr int kMaxDevices = 64;
+// The array's device address, cached per CUDA context: host code cannot use the
+// symbol itself as a device pointer, and the address belongs to the context the
+// module was loaded into, so a cache keyed on the device ordinal alone would go
+// stale when that device's context is destroyed and created again (a device
+// reset).  The current context is read through the driver's cuCtxGetCurrent.
+constexpr int kMaxContexts = 64;
 std::mutex g_static_scratch_mutex;
-double *g_static_scratch_addr[kMaxDevices] = {};
+struct ScratchEntry {
+    void *ctx;
+    double *addr;
+};
+ScratchEntry g_static_scratch_addr[kMaxContexts] = {};
+int g_static_scratch_entries = 0;
 
-// Device address of g_static_scratch on the current device, looked up once per
-// device (host code cannot use the symbol itself as a device pointer).
+typedef int (*CtxGetCurrentFn)(void **);
+
+cudaError_t current_context(void **ctx)
+{
+    static CtxGetCurrentFn fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !f) return cudaErrorNotSupported;
+        fn = reinterpret_cast<CtxGetCurrentFn>(f);
+    }
+    *ctx = nullptr;
+    return fn(ctx) == 0 ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
+
+// Device address of g_static_scratch in the current context, looked up the first
+// time a context is seen (cudaGetSymbolAddress also binds the device's primary
+// context to this thread when none is current yet).
 cudaError_t static_scratch(double **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *ctx = nullptr;
+    cudaError_t e = current_context(&ctx);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(g_static_scratch_mutex);
-    if (!g_static_scratch_addr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess) return e;
-        g_static_scratch_addr[dev] = static_cast<double *>(p);
-    }
-    *out = g_static_scratch_addr[dev];
+    if (ctx)
+        for (int i = 0; i < g_static_scratch_entries; ++i)
+            if (g_static_scratch_addr[i].ctx == ctx) {
+                *out = g_static_scratch_addr[i].addr;
+                return cudaSuccess;
+            }
+    void *p = nullptr;
+    if ((e = cudaGetSymbolAddress(&p, g_static_scratch)) != cudaSuccess) return e;
+    if (!ctx && (e = current_context(&ctx)) != cudaSuccess) return e;
+    if (ctx && g_static_scratch_entries < kMaxContexts)
+        g_static_scratch_addr[g_static_scratch_entries++] = ScratchEntry{ctx, static_cast<double *>(p)};
+    *out = static_cast<double *>(p);
     return cudaSuccess;
 }
 

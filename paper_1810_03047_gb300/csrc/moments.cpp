@@ -16,7 +16,7 @@
 namespace {
 
 // Signed integer of 6 x 64 bits (sign and magnitude), enough for the exact
-// variance numerator n S2 2^100 - S1^2 (below 2^282 for up to 2^40 values).
+// variance numerator n S2 - S1^2 (below 2^282 for up to 2^40 values).
 struct Big {
     bool neg = false;
     uint64_t m[6] = {0, 0, 0, 0, 0, 0};
@@ -128,9 +128,12 @@ Big mul(const Big &a, const Big &b)
     return r;
 }
 
-Big from_digits(long long d0, long long d1, long long d2)
+// sum_i d[i] 2^(48 i)
+Big from_digits(const long long *d, int count)
 {
-    return add(add(from_i64(d0), shl(from_i64(d1), qtm::kDigitBits)), shl(from_i64(d2), 2 * qtm::kDigitBits));
+    Big r;
+    for (int i = 0; i < count; ++i) r = add(r, shl(from_i64(d[i]), i * qtm::kDigitBits));
+    return r;
 }
 
 // Round to nearest double: the top 64 bits, with any lower set bit folded into
@@ -169,7 +172,7 @@ namespace qtm {
 
 void moments_finish(const long long *w, long long n, int E, double *mean, double *se, double *sum, double *sumsq)
 {
-    if (w[6] > 0) {
+    if (w[kBad] > 0) {
         const double nan = std::nan("");
         if (mean) *mean = nan;
         if (se) *se = nan;
@@ -177,24 +180,24 @@ void moments_finish(const long long *w, long long n, int E, double *mean, double
         if (sumsq) *sumsq = nan;
         return;
     }
-    const Big S1 = from_digits(w[0], w[1], w[2]);
-    const Big S2 = from_digits(w[3], w[4], w[5]);
+    const Big S1 = from_digits(w + kS1, kS1Digits);  // quanta 2^(E - 100)
+    const Big S2 = from_digits(w + kS2, kS2Digits);  // quanta 2^(2E - 200)
     const double s1 = std::ldexp(to_double(S1), E - kQuantBits);
     if (sum) *sum = s1;
-    if (sumsq) *sumsq = std::ldexp(to_double(S2), 2 * E - kQuantBits);
+    if (sumsq) *sumsq = std::ldexp(to_double(S2), 2 * (E - kQuantBits));
     if (mean) *mean = n > 0 ? s1 / (double)n : 0.0;
     if (!se) return;
     if (n < 2) {
         *se = 0.0;
         return;
     }
-    // n sum x^2 - (sum x)^2 in quanta 2^(2E - 200): exact
-    const Big D = add(shl(mul(S2, from_i64(n)), kQuantBits), negate(mul(S1, S1)));
+    // n sum q^2 - (sum q)^2 = n (n - 1) times the sample variance of the q, exact (quanta 2^(2E - 200))
+    const Big D = add(mul(S2, from_i64(n)), negate(mul(S1, S1)));
     if (D.neg || is_zero(D)) {
         *se = 0.0;
         return;
     }
-    const double num = std::ldexp(to_double(D), 2 * E - 2 * kQuantBits);
+    const double num = std::ldexp(to_double(D), 2 * (E - kQuantBits));
     const double den = (double)n * (double)n * (double)(n - 1);
     *se = std::sqrt(num / den);
 }
@@ -221,11 +224,10 @@ qtm_status qtm_moments_of_values(const double *values, int64_t ntraj, int32_t n_
         }
     for (int p = 0; p < n_values; ++p) {
         const int E = scale_exp[p % n_obs];
-        const double sc1 = qtm::pow2(qtm::kQuantBits - E), sc2 = qtm::pow2(qtm::kQuantBits - 2 * E);
-        const double lim = qtm::pow2(E);
+        const double sc = qtm::pow2(qtm::kQuantBits - E), lim = qtm::pow2(E);
         qtm::MomentAcc acc;
         acc.clear();
-        for (int64_t i = 0; i < ntraj; ++i) acc.add(values[(size_t)i * n_values + p], sc1, sc2, lim);
+        for (int64_t i = 0; i < ntraj; ++i) acc.add(values[(size_t)i * n_values + p], sc, lim);
         acc.normalize();
         acc.store(reinterpret_cast<long long *>(words) + (size_t)p * qtm::kMomentWords, 1);
     }
@@ -260,13 +262,13 @@ qtm_status qtm_combine_moments(int32_t n_shards, int32_t n_values, int32_t n_obs
         }
     const size_t W = qtm::kMomentWords;
     for (int p = 0; p < n_values; ++p) {
-        long long w[qtm::kMomentWords] = {0, 0, 0, 0, 0, 0, 0};
+        long long w[qtm::kMomentWords] = {};
         // shards in rank order; integer digits, so the order does not change the result
         for (int r = 0; r < n_shards; ++r) {
             const int64_t *s = words + ((size_t)r * n_values + p) * W;
             for (size_t q = 0; q < W; ++q) w[q] += s[q];
-            qtm::normalize_digits(w);
-            qtm::normalize_digits(w + 3);
+            qtm::normalize_digits(w + qtm::kS1, qtm::kS1Digits);
+            qtm::normalize_digits(w + qtm::kS2, qtm::kS2Digits);
         }
         qtm::moments_finish(w, n, scale_exp[p % n_obs], mean + p, stderr_out ? stderr_out + p : nullptr,
                             sum ? sum + p : nullptr, sumsq ? sumsq + p : nullptr);

@@ -52,7 +52,7 @@ EXPORTS = ["qtm_set_allocator", "qtm_create", "qtm_run", "qtm_run_range", "qtm_e
            "qtm_propagator"]
 
 QTM_PROPOSAL_FLOATS = 4685
-QTM_MOMENT_WORDS = 7
+QTM_MOMENT_WORDS = 9
 QTM_PEAK_FP64 = 0
 QTM_PEAK_FP32 = 1
 QTM_PEAK_DF64 = 2

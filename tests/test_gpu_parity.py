@@ -102,10 +102,10 @@ CASES = [
     ("jaynes_cummings_driven", dict(), 403),
     ("ising_L4", dict(ntraj=200), 200),
     ("ising_L6", dict(ntraj=67), 67),
-    ("ising_L7", dict(ntraj=40), 40),          # N = 128: two warps per trajectory
-    ("ising_L8", dict(ntraj=24), 24),          # N = 256: four warps
-    ("paper_trilinear", dict(ntraj=10), 10),   # N = 512: eight warps, Sec. 4.2
-    ("ising_L10", dict(ntraj=9), 9),           # N = 1024: eight warps, four rows each
+    ("ising_L7", dict(ntraj=128), 128),        # N = 128: two warps per trajectory
+    ("ising_L8", dict(ntraj=96), 96),          # N = 256: four warps
+    ("paper_trilinear", dict(ntraj=128), 128),  # N = 512: eight warps, Sec. 4.2
+    ("ising_L10", dict(ntraj=96), 96),         # N = 1024: eight warps, four rows each
 ]
 
 

@@ -69,8 +69,9 @@ def test_network_improves_on_constant_rate_estimate(trained):
 
 
 def test_proposal_keeps_jumps_and_reports_gain(trained, capsys):
-    """The root find still decides: with the proposal on, the same jumps happen at
-    the same times up to the integration tolerance; only the step sequence changes.
+    """The root find still decides: with the proposal on, every trajectory makes
+    the same jumps through the same channels at the same times up to the
+    integration tolerance; only the step sequence changes.
 
     The step count is reported, not required to fall.  With a continuous
     extension the step that contains a crossing is kept up to the crossing and
@@ -82,16 +83,15 @@ def test_proposal_keeps_jumps_and_reports_gain(trained, capsys):
     n = 2000
     off = _run(prob, n, 1, False, params=params)
     on = _run(prob, n, 1, True, params=params)
-    same = on["n_jumps"] == off["n_jumps"]
-    assert same.mean() >= 0.98
-    for i in np.where(same)[0][:500]:
+    np.testing.assert_array_equal(on["n_jumps"], off["n_jumps"])
+    for i in range(n):
         k = min(int(off["n_jumps"][i]), 64)
-        assert np.array_equal(on["jump_ch"][i, :k], off["jump_ch"][i, :k]) or k == 0 or i < 0
+        np.testing.assert_array_equal(on["jump_ch"][i, :k], off["jump_ch"][i, :k])
         dt = np.abs(on["jump_t"][i, :k] - off["jump_t"][i, :k])
-        assert np.all(dt <= 1e-4 * np.maximum(1.0, off["jump_t"][i, :k])), (i, dt.max())
-    # ensemble: same within the statistics of the few trajectories whose jump
-    # crossed an output time
-    assert np.abs(on["mean"] - off["mean"]).max() <= 0.02
+        assert np.all(dt <= 1e-6 * np.maximum(1.0, off["jump_t"][i, :k])), (i, dt.max())
+    # the two step sequences move jump times by ~rtol; an output flips only where a
+    # jump time crosses an output time, which none does here
+    assert np.abs(on["mean"] - off["mean"]).max() <= 1e-5
     s_off = off["stats"]["accepted"] + off["stats"]["rejected"]
     s_on = on["stats"]["accepted"] + on["stats"]["rejected"]
     with capsys.disabled():
@@ -99,6 +99,56 @@ def test_proposal_keeps_jumps_and_reports_gain(trained, capsys):
               f"({100 * (s_off - s_on) / s_off:+.2f} %), loss {trained['loss']:.4f} vs "
               f"rate estimate {trained['base']:.4f}")
     assert s_on <= 1.02 * s_off
+
+
+# Bars against the exact oracle at rtol 1e-10, atol 1e-12.  Measured on the CPU,
+# the Dormand-Prince oracle itself meets them with room: on the first 200 JC
+# trajectories identical jumps and channels, jump times within 8.7e-10 relative
+# (median 2.4e-11), outputs within 1.3e-7, ensemble 1.6e-9.  The proposal-on and
+# proposal-off GPU runs are held to the same bars.
+EXACT_NTRAJ = 160
+EXACT_TAU_MAX = 5e-9      # every jump time, relative to max(1, tau)
+EXACT_TAU_MEDIAN = 2e-10
+EXACT_OBS = 1e-6          # every per-trajectory output
+EXACT_ENSEMBLE = 1e-8
+
+
+@pytest.fixture(scope="module")
+def exact_jc():
+    from oracle import exact, oracle
+    prob = S.jaynes_cummings_driven().with_(rtol=1e-10, atol=1e-12)
+    o = exact.mcwf(prob, ntraj=EXACT_NTRAJ, max_jumps=64)
+    o["mean"], _ = oracle.ensemble(o["obs"])
+    return prob, o
+
+
+@pytest.mark.parametrize("prec", [Q.QTM_PREC_C128, Q.QTM_PREC_DF64])
+@pytest.mark.parametrize("proposal", [False, True])
+def test_proposal_path_against_the_exact_oracle(trained, exact_jc, prec, proposal):
+    """The proposal-on kernels against the exact trajectory (expm between jumps,
+    brentq for the crossing), trajectory by trajectory, at the same bars as the
+    proposal-off kernels: the learned step choice leaves every jump decision to
+    the root find and changes results only within the integration tolerance."""
+    prob, ex = exact_jc
+    ctx = Q.qtm_create(prob, precision=prec, record_jumps=64)
+    Q.qtm_proposal_set(ctx, trained["params"])
+    Q.qtm_proposal_enable(ctx, proposal)
+    Q.qtm_run(ctx, EXACT_NTRAJ, prob.seed)
+    mean, _ = Q.qtm_expect(ctx)
+    obs = Q.qtm_traj_expect(ctx)
+    nj, jt, jc = Q.qtm_jumps(ctx)
+    Q.qtm_destroy(ctx)
+    np.testing.assert_array_equal(nj, ex["n_jumps"])
+    rel = []
+    for i in range(EXACT_NTRAJ):
+        k = min(int(nj[i]), 64)
+        np.testing.assert_array_equal(jc[i, :k], ex["jump_ch"][i, :k])
+        rel.append(np.abs(jt[i, :k] - ex["jump_t"][i, :k]) / np.maximum(1.0, ex["jump_t"][i, :k]))
+    rel = np.concatenate(rel)
+    assert rel.max() <= EXACT_TAU_MAX, rel.max()
+    assert np.median(rel) <= EXACT_TAU_MEDIAN, np.median(rel)
+    assert np.abs(obs - ex["obs"]).max() <= EXACT_OBS
+    assert np.abs(mean - ex["mean"]).max() <= EXACT_ENSEMBLE
 
 
 def test_proposal_refused_where_it_is_not_compiled():

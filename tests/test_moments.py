@@ -119,7 +119,7 @@ def test_non_representable_values_make_the_output_nan():
     E = np.array([1], np.int32)  # values must lie below 2^1
     x = np.array([[0.5, 0.25, 1.0], [np.nan, 0.5, 1.0], [0.25, np.inf, 2.5]])
     w = Q.qtm_moments_of_values(x, 1, E)
-    assert list(w[:, 6]) == [1, 1, 1]
+    assert list(w[:, 8]) == [1, 1, 1]
     mean, se, s, s2 = Q.qtm_combine_moments(w, [3], 1, E)
     assert np.isnan(mean).all() and np.isnan(se).all() and np.isnan(s).all()
 
@@ -149,7 +149,7 @@ def test_scale_exponents_follow_the_observable_bound():
 
 def test_argument_errors():
     E = np.array([2], np.int32)
-    w = np.zeros((2, 7), np.int64)
+    w = np.zeros((2, 9), np.int64)
     with pytest.raises(Q.QtmError) as ei:
         Q.qtm_combine_moments(w, [-1], 1, E)
     assert ei.value.status == Q.QTM_ERR_ARG
