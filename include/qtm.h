@@ -161,6 +161,8 @@ typedef struct {
     int32_t reserved;
     double kernel_ms;          /* device time of the trajectory kernel (CUDA events on the context stream) */
     double reduce_ms;          /* device time of the ensemble reduction */
+    int64_t proposal_misses;   /* exponential method with the learned proposal: crossings whose predicted
+                                  bracket missed (the search then descended as without a prediction) */
 } qtm_stats_t;
 
 typedef struct qtm_ctx qtm_ctx;
@@ -345,6 +347,20 @@ qtm_status qtm_jumps(qtm_ctx *ctx, int32_t *n_jumps, double *jump_t, int32_t *ju
  * of the continuous extension still decides every jump; only the step sequence
  * changes (so results move by the integration tolerance, not more).  The paper
  * has no such component: it is the learned part of this library's design.
+ *
+ * Under the exponential method (qtm_set_method) the proposal acts inside the
+ * crossing search instead: once an output interval is known to contain the
+ * crossing, the features are taken over that interval (the decay rate from the
+ * norms at its two ends, its change since the previous interval, the norm at
+ * its start, log r, the latest two outputs), the network corrects the
+ * constant-rate estimate of the crossing time, and the search first tries the
+ * ladder bracket of width delta that holds the prediction -- formed with the
+ * binary digits of its start, which are exactly the levels the plain descent
+ * would keep -- and checks it with one product.  On a hit the crossing is found
+ * from the same state, bit for bit, with fewer products; on a miss the plain
+ * descent takes over (qtm_stats_t.proposal_misses counts them).  Pairs for this
+ * use are collected by qtm_proposal_collect on a context that uses the
+ * exponential method (one record per crossing).
  * Supported for QTM_PREC_C128 and QTM_PREC_DF64 at dimension <= 64 (the
  * single-warp lane layouts, where it is compiled into separate kernels so the
  * plain kernels carry none of it); other contexts get QTM_ERR_UNSUPPORTED from
@@ -358,7 +374,10 @@ qtm_status qtm_jumps(qtm_ctx *ctx, int32_t *n_jumps, double *jump_t, int32_t *ju
 /* Runs trajectories 0 .. ntraj-1 of the plain method (proposal off) and records,
  * every `stride` accepted steps and at most max_per_traj times per trajectory,
  * the 6 raw features and the time left to the next jump; records of a
- * trajectory's last jump interval (no jump followed) are dropped.  Keeps the
+ * trajectory's last jump interval (no jump followed) are dropped.  Under the
+ * exponential method a record is taken at every `stride`-th crossing, with the
+ * features of the output interval that contains it and the time from the
+ * interval's start to the crossing.  Keeps the
  * pairs for qtm_proposal_train; *npairs (may be NULL) = their number.
  * Synchronises; the run's observables are available as after qtm_run. */
 qtm_status qtm_proposal_collect(qtm_ctx *ctx, int64_t ntraj, uint64_t seed, int32_t stride,
@@ -463,7 +482,9 @@ qtm_status qtm_rhs_batch(qtm_ctx *ctx, int64_t n_vec, const double *y, double *m
  * QTM_PREC_C128, QTM_PREC_DF64 or QTM_PREC_C64 (FP32 propagators and state,
  * double-float norms: a trajectory's jump times move by about the FP32 rounding
  * accumulated over the products), dimension <= 256 and no time-dependent terms
- * (QTM_ERR_UNSUPPORTED otherwise; the learned proposal is refused by qtm_run).  QTM_METHOD_DOPRI5 restores the default.
+ * (QTM_ERR_UNSUPPORTED otherwise).  The learned proposal works with it on the
+ * contexts that support the proposal (complex128 or double-float, dimension <= 64;
+ * see above).  QTM_METHOD_DOPRI5 restores the default.
  * QTM_ERR_ARG for any other value. */
 qtm_status qtm_set_method(qtm_ctx *ctx, int32_t method);
 

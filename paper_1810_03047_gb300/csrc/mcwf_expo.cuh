@@ -107,7 +107,7 @@ struct Expo {
     CsrView<Ar> M;
     cplx *A, *B, *U;
     const typename Ar::coef *inv;  // inv[m] = 1/m in the coefficient type (shared memory)
-    unsigned long long n_rhs = 0, n_rej = 0;
+    unsigned long long n_rhs = 0, n_rej = 0, n_miss = 0;
     int root_iters = 0;
 
     __device__ const cplx *level(int l) const
@@ -211,25 +211,72 @@ struct Expo {
 
     // (B) with ||psi||^2 = nb >= r now and ||exp(d M) psi||^2 < r: the time s in
     // (0, d] of the crossing; psi(s) is left in *out (A or B, synchronised).
-    __device__ double crossing(double d, const cplx *psi, double nb, double r, double t0, cplx **out)
+    // s_hat >= 0 is a predicted crossing time (the learned proposal): the bracket
+    // [m delta, (m + 1) delta) holding it is formed directly from the binary digits
+    // of m -- the same products, in the same order, as the levels the descent keeps
+    // for that bracket -- and checked with one more product; on a miss the descent
+    // takes over.  The crossing itself is found as without a prediction.
+    __device__ double crossing(double d, const cplx *psi, double nb, double r, double t0, cplx **out,
+                              double s_hat = -1.0)
     {
         const int L = a.expo_levels - 1;
         const double delta = a.expo_delta;
         const cplx *base = psi;
         double cur = 0.0;
-        // binary descent: keep level l when the norm after it is still >= r
+        bool bracketed = false;
+        if (s_hat >= 0.0) {
+            const double mmax = ceil(d / delta) - 1.0;
+            double md = floor(s_hat / delta);
+            if (md > mmax) md = mmax;
+            if (md < 0.0) md = 0.0;
+            const unsigned long long m = (unsigned long long)md;
+            double nm = nb;
 #pragma unroll 1
-        for (int l = L; l >= 0; --l) {
-            const double step = ldexp(delta, l);
-            if (cur + step > d) continue;
-            cplx *o = (base == A) ? B : A;
-            const double nn = apply_level(l, base, o);
-            if (nn >= r) {
-                base = o;
-                cur += step;
-                nb = nn;
-            } else {
-                ++n_rej;
+            for (int l = L; l >= 0; --l)
+                if ((m >> l) & 1ULL) {
+                    cplx *o = (base == A) ? B : A;
+                    nm = apply_level(l, base, o);
+                    base = o;
+                }
+            if (nm >= r) {
+                cur = md * delta;
+                nb = nm;
+                if (cur + delta >= d) {
+                    bracketed = true;  // the interval ends inside the last delta
+                } else {
+                    cplx *o = (base == A) ? B : A;
+                    const double n1 = apply_level(0, base, o);
+                    if (n1 < r) {
+                        bracketed = true;
+                        ++n_rej;
+                    } else {  // the crossing lies later: descend from the end of this delta
+                        base = o;
+                        cur += delta;
+                        nb = n1;
+                        ++n_miss;
+                    }
+                }
+            } else {  // the crossing lies earlier: descend from psi
+                base = psi;
+                ++n_miss;
+            }
+        }
+        // binary descent: keep level l when the norm after it is still >= r (a
+        // level ending at d would not be kept: the norm there is below r)
+        if (!bracketed) {
+#pragma unroll 1
+            for (int l = L; l >= 0; --l) {
+                const double step = ldexp(delta, l);
+                if (cur + step >= d) continue;
+                cplx *o = (base == A) ? B : A;
+                const double nn = apply_level(l, base, o);
+                if (nn >= r) {
+                    base = o;
+                    cur += step;
+                    nb = nn;
+                } else {
+                    ++n_rej;
+                }
             }
         }
         double smax = d - cur;
@@ -340,6 +387,25 @@ struct Expo {
     }
 };
 
+// The learned proposal in the exponential method (instantiations with
+// kFeatProposal; single-warp groups, one trajectory per group).  When an output
+// interval (t_{j-1}, t_j] is found to contain the crossing, the features are the
+// decay rate over that interval from the norms at its ends, Gamma = log(nb/nn)/d,
+// its change since the previous interval's rate (per unit time), the norm nb at
+// t_{j-1}, log r, and the latest outputs of the first two observables; the network
+// corrects the constant-rate estimate log(nb/r)/Gamma of the time to the crossing
+// (the same parametrisation as the Dormand-Prince proposal), and the prediction
+// selects the bracket the crossing search tries first.  In collection mode
+// (rec_stride > 0) every rec_stride-th crossing stores its features and, once the
+// crossing is found, its time from t_{j-1}.
+struct ExpoProp {
+    float h[kMlpHidden];  // the network's hidden-layer scratch
+    float f[kMlpIn];      // features of the current crossing
+    float gam_prev;       // decay rate of the last jump-free interval (< 0: none yet)
+    int rec_n;            // records stored for this trajectory
+};
+constexpr int kExpoPropStride = (int)((sizeof(ExpoProp) + 15) & ~size_t(15));
+
 // Per-trajectory scalars of a group (indexed at run time; they live in local memory).
 struct ExpoTraj {
     double t, r, c, nb;
@@ -349,10 +415,13 @@ struct ExpoTraj {
 };
 
 // Trajectories il0 .. il0 + live - 1 (live <= T) of the launch, in lock step.
-template <class Ar, int G, int R, int T>
+template <class Ar, int G, int R, int T, int FEAT>
 __device__ void run_group_expo(const KernelArgs &a, const Group<G> &g, const int *si, const typename Ar::real *sv,
-                               const typename Ar::coef *inv, typename Ar::cplx *slots, long long il0, int live)
+                               const typename Ar::coef *inv, typename Ar::cplx *slots, long long il0, int live,
+                               ExpoProp *PS)
 {
+    constexpr bool PROP = (FEAT & kFeatProposal) != 0;
+    static_assert(!PROP || T == 1, "the proposal takes one trajectory per group");
     using cplx = typename Ar::cplx;
     using S = ExpoSlots<T>;
     constexpr int NP = G * R;
@@ -385,8 +454,14 @@ __device__ void run_group_expo(const KernelArgs &a, const Group<G> &g, const int
         x.jdone = a.n_t;
         x.n_jump = 0;
         record_outputs<Ar, G, R>(a, g, si, sv, psi_all + t * NP, 0, a.out + (size_t)(il0 + t) * a.n_t * a.n_obs,
-                                 nullptr);
+                                 PROP ? PS->f + 4 : nullptr);
         x.nb = E.norm2(psi_all + t * NP);
+    }
+    if constexpr (PROP) {
+        if (gl == 0) {
+            PS->gam_prev = -1.f;
+            PS->rec_n = 0;
+        }
     }
 #pragma unroll 1
     for (int j = 1; j < a.n_t; ++j) {
@@ -429,7 +504,34 @@ __device__ void run_group_expo(const KernelArgs &a, const Group<G> &g, const int
                 }
                 // (B): the norm reaches r inside (x.t, t_j]
                 cplx *ytau = nullptr;
-                const double s = E.crossing(a.t[j] - x.t, psi, x.nb, x.r, x.t, &ytau);
+                const double d = a.t[j] - x.t;
+                double s_hat = -1.0;
+                float *rec = nullptr;
+                if constexpr (PROP) {
+                    // features (lane 0 writes them; mlp_eval synchronises before reading)
+                    const float gam = (float)(log(x.nb / nn) / d);
+                    if (gl == 0) {
+                        PS->f[0] = gam;
+                        PS->f[1] = PS->gam_prev > 0.f ? (gam - PS->gam_prev) / (float)d : 0.f;
+                        PS->f[2] = (float)x.nb;
+                        PS->f[3] = __logf((float)x.r);
+                        if (a.rec_stride > 0 && (long long)(x.n_jump % a.rec_stride) == 0 && PS->rec_n < a.rec_max) {
+                            rec = a.rec + ((size_t)(il0 + t) * a.rec_max + PS->rec_n++) * kRecFloats;
+                            for (int q = 0; q < kMlpIn; ++q) rec[q] = PS->f[q];
+                            rec[6] = 0.f;
+                        }
+                    }
+                    if (a.mlp) {
+                        const float y = mlp_eval<G>(g, a.mlp, PS->f, PS->h);
+                        const double est = (log(x.nb) - log(x.r)) / (double)gam;
+                        s_hat = est * (double)__expf(y);
+                        if (!(s_hat >= 0.0)) s_hat = 0.0;
+                        if (s_hat > d) s_hat = d;
+                    }
+                }
+                const double s = E.crossing(d, psi, x.nb, x.r, x.t, &ytau, s_hat);
+                if constexpr (PROP)
+                    if (rec) rec[7] = (float)s;
                 double tau = x.t + s;
                 if (tau > a.t[j]) tau = a.t[j];
                 // (C)
@@ -450,6 +552,8 @@ __device__ void run_group_expo(const KernelArgs &a, const Group<G> &g, const int
                 jump_draws(a.seed, a.traj0 + il0 + t, x.k, x.r, x.c);
                 x.t = tau;
                 x.nb = 1.0;
+                if constexpr (PROP)
+                    if (gl == 0) PS->gam_prev = -1.f;
                 y = E.propagate(a.t[j] - tau, psi);
                 nn = E.norm2(y);
             }
@@ -457,7 +561,10 @@ __device__ void run_group_expo(const KernelArgs &a, const Group<G> &g, const int
                 x.jdone = j;
                 continue;
             }
-            record_outputs<Ar, G, R>(a, g, si, sv, y, j, a.out + (size_t)(il0 + t) * a.n_t * a.n_obs, nullptr);
+            if constexpr (PROP)  // the decay rate over this (jump-free) stretch, for the next crossing's features
+                if (gl == 0) PS->gam_prev = (float)(log(x.nb / nn) / (a.t[j] - x.t));
+            record_outputs<Ar, G, R>(a, g, si, sv, y, j, a.out + (size_t)(il0 + t) * a.n_t * a.n_obs,
+                                     PROP ? PS->f + 4 : nullptr);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int row = gl + G * r;
@@ -492,6 +599,7 @@ __device__ void run_group_expo(const KernelArgs &a, const Group<G> &g, const int
         atomicAdd(&a.counters[kRhs], E.n_rhs);
         atomicAdd(&a.counters[kJumps], jumps);
         atomicAdd(&a.counters[kRootIters], (unsigned long long)E.root_iters);
+        if constexpr (PROP) atomicAdd(&a.counters[kPropMiss], E.n_miss);
     }
 }
 
@@ -509,7 +617,7 @@ __host__ __device__ constexpr int expo_batch() { return 1; }
 
 // Multi-warp groups: two CTAs per SM (the register bound keeps a second CTA
 // resident; one CTA per SM halved the dense complex64 throughput).
-template <class Ar, int G, int R, int BLOCK>
+template <class Ar, int G, int R, int BLOCK, int FEAT>
 __global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 2)) mcwf_expo_kernel(const __grid_constant__ KernelArgs a)
 {
     using cplx = typename Ar::cplx;
@@ -537,17 +645,20 @@ __global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 2)) mcwf_expo_kernel(con
     const Group<G> g(threadIdx.x, reinterpret_cast<unsigned long long *>(smem + a.smem_scratch_offset));
     cplx *slots = reinterpret_cast<cplx *>(smem + a.smem_ybuf_offset) +
                   (size_t)(threadIdx.x / G) * ExpoSlots<T>::kCount * (G * R);
+    ExpoProp *PS = (FEAT & kFeatProposal)
+                       ? reinterpret_cast<ExpoProp *>(smem + a.smem_mlp_offset + (size_t)(threadIdx.x / G) * kExpoPropStride)
+                       : nullptr;
     for (;;) {
         unsigned long long i = 0;
         if (g.gl == 0) i = atomicAdd(a.queue, (unsigned long long)T);
         i = g.bcast0(i);
         if ((long long)i >= a.ntraj) break;
         const long long left = a.ntraj - (long long)i;
-        run_group_expo<Ar, G, R, T>(a, g, si, sv, inv, slots, (long long)i, left < T ? (int)left : T);
+        run_group_expo<Ar, G, R, T, FEAT>(a, g, si, sv, inv, slots, (long long)i, left < T ? (int)left : T, PS);
     }
 }
 
-template <class Ar, int G, int R>
+template <class Ar, int G, int R, int FEAT = 0>
 cudaError_t launch_expo_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInfo *info)
 {
     using cplx = typename Ar::cplx;
@@ -560,13 +671,15 @@ cudaError_t launch_expo_instance(const KernelArgs &a0, cudaStream_t stream, Laun
     const size_t vb = ops_in_shared<G>() ? al16((size_t)a.n_vals * sizeof(typename Ar::real)) : 0;
     const size_t sb = al16((size_t)GROUPS * (Group<G>::kWarps + 1) * 8);
     const size_t cb = al16((kExpoTaylor + 1) * sizeof(typename Ar::coef));
+    const size_t mb = (FEAT & kFeatProposal) ? (size_t)GROUPS * kExpoPropStride : 0;
     a.smem_vals_offset = (int)ib;
     a.smem_scratch_offset = (int)(ib + vb);
     a.smem_coef_offset = (int)(ib + vb + sb);
-    a.smem_ybuf_offset = (int)(ib + vb + sb + cb);
-    const size_t smem = ib + vb + sb + cb + (size_t)GROUPS * ExpoSlots<T>::kCount * G * R * sizeof(cplx);
+    a.smem_mlp_offset = (int)(ib + vb + sb + cb);
+    a.smem_ybuf_offset = (int)(ib + vb + sb + cb + mb);
+    const size_t smem = ib + vb + sb + cb + mb + (size_t)GROUPS * ExpoSlots<T>::kCount * G * R * sizeof(cplx);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
-    auto kern = mcwf_expo_kernel<Ar, G, R, BLOCK>;
+    auto kern = mcwf_expo_kernel<Ar, G, R, BLOCK, FEAT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, nb = 0;
@@ -605,6 +718,23 @@ cudaError_t launch_expo(const KernelArgs &a, cudaStream_t stream, LaunchInfo *in
     if (a.G == 32 && a.R == 4) return launch_expo_instance<Ar, 32, 4>(a, stream, info);
     if (a.G == 128 && a.R == 2) return launch_expo_instance<Ar, 128, 2>(a, stream, info);
     if (a.G == 64 && a.R == 4) return launch_expo_instance<Ar, 64, 4>(a, stream, info);
+    return cudaErrorInvalidValue;
+}
+
+// The same with the learned proposal compiled in (single-warp layouts, dimension <= 64).
+template <class Ar>
+cudaError_t launch_expo_prop(const KernelArgs &a, cudaStream_t stream, LaunchInfo *info)
+{
+    constexpr int F = kFeatProposal;
+    if (a.G == 1 && a.R == 2) return launch_expo_instance<Ar, 1, 2, F>(a, stream, info);
+    if (a.G == 4 && a.R == 2) return launch_expo_instance<Ar, 4, 2, F>(a, stream, info);
+    if (a.G == 8 && a.R == 2) return launch_expo_instance<Ar, 8, 2, F>(a, stream, info);
+    if (a.G == 4 && a.R == 4) return launch_expo_instance<Ar, 4, 4, F>(a, stream, info);
+    if (a.G == 16 && a.R == 2) return launch_expo_instance<Ar, 16, 2, F>(a, stream, info);
+    if (a.G == 8 && a.R == 4) return launch_expo_instance<Ar, 8, 4, F>(a, stream, info);
+    if (a.G == 32 && a.R == 2) return launch_expo_instance<Ar, 32, 2, F>(a, stream, info);
+    if (a.G == 16 && a.R == 4) return launch_expo_instance<Ar, 16, 4, F>(a, stream, info);
+    if (a.G == 32 && a.R == 4) return launch_expo_instance<Ar, 32, 4, F>(a, stream, info);
     return cudaErrorInvalidValue;
 }
 

@@ -98,10 +98,17 @@ template <class Ar, int G>
 __device__ __forceinline__ typename Ar::cplx spmv_row(const CsrView<Ar> &A, const typename Ar::cplx *x, int gl,
                                                       int r)
 {
-    typename Ar::acc acc = Ar::zero();
+    typename Ar::acc acc;
     int off = A.tab_re[2 * r] + gl, w = A.tab_re[2 * r + 1];
+    int t0 = 0;
+    if (w > 0) {  // the first product starts the accumulator (the same bits as adding it to zero)
+        acc = Ar::first_re(A.val_re[off], x[A.col_re[off]]);
+        t0 = 1;
+    } else {
+        acc = Ar::zero();
+    }
 #pragma unroll 1
-    for (int t = 0; t < w; ++t) Ar::mac_re(acc, A.val_re[off + t * G], x[A.col_re[off + t * G]]);
+    for (int t = t0; t < w; ++t) Ar::mac_re(acc, A.val_re[off + t * G], x[A.col_re[off + t * G]]);
     off = A.tab_im[2 * r] + gl;
     w = A.tab_im[2 * r + 1];
 #pragma unroll 1
@@ -312,6 +319,54 @@ static __device__ __noinline__ void prop_jumped(const KernelArgs &a, PropState *
     prop_interval(P, tau, r);
 }
 
+// The first theta in (0, 1] with f(theta) = sum_s P_s theta^s = 0, f(0) > 0: the
+// first of eight sub-intervals whose right end has f < 0 brackets the root, then
+// Newton's method with a bisection safeguard (FP64).  1 when f stays >= 0.
+static __device__ __noinline__ double first_root(const double (&P)[11], int &iters)
+{
+    auto poly = [&](double x) {
+        double f = P[10];
+#pragma unroll
+        for (int s = 9; s >= 0; --s) f = fma(f, x, P[s]);
+        return f;
+    };
+    double lo = 0.0, hi = 1.0;
+    bool found = false;
+    for (int i = 1; i <= 8; ++i) {
+        const double x = i / 8.0;
+        if (poly(x) < 0.0) {
+            lo = (i - 1) / 8.0;
+            hi = x;
+            found = true;
+            break;
+        }
+    }
+    if (!found) return 1.0;
+    double x = 0.5 * (lo + hi);
+    for (int it = 0; it < 100; ++it) {
+        ++iters;
+        double f = P[10], df = 0.0;
+#pragma unroll
+        for (int s = 9; s >= 0; --s) {
+            df = fma(df, x, f);
+            f = fma(f, x, P[s]);
+        }
+        if (f == 0.0) break;
+        if (f < 0.0)
+            hi = x;
+        else
+            lo = x;
+        double xn = x - f / df;
+        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+        if (fabs(xn - x) <= 1e-15 || hi - lo <= 1e-15) {
+            x = xn;
+            break;
+        }
+        x = xn;
+    }
+    return x;
+}
+
 // First theta in (0, 1] where ||y(theta)||^2 = r.  ||y(theta)||^2 = sum_s P_s theta^s
 // with y(theta) = sum_m theta^m u_m, u_0 = psi, u_m = h sum_j W(j, m) K_j, and
 // P_s = sum_{m + m' = s} Re<u_m, u_m'>.
@@ -358,47 +413,7 @@ __device__ __noinline__ double locate_crossing(const Coefs<Ar> &C, Lanes<Ar, G, 
             }
     }
     P[0] -= r;
-    auto poly = [&](double x) {
-        double f = P[10];
-#pragma unroll
-        for (int s = 9; s >= 0; --s) f = fma(f, x, P[s]);
-        return f;
-    };
-    double lo = 0.0, hi = 1.0;
-    bool found = false;
-    for (int i = 1; i <= 8; ++i) {
-        const double x = i / 8.0;
-        if (poly(x) < 0.0) {
-            lo = (i - 1) / 8.0;
-            hi = x;
-            found = true;
-            break;
-        }
-    }
-    if (!found) return 1.0;
-    double x = 0.5 * (lo + hi);
-    for (int it = 0; it < 100; ++it) {
-        ++iters;
-        double f = P[10], df = 0.0;
-#pragma unroll
-        for (int s = 9; s >= 0; --s) {
-            df = fma(df, x, f);
-            f = fma(f, x, P[s]);
-        }
-        if (f == 0.0) break;
-        if (f < 0.0)
-            hi = x;
-        else
-            lo = x;
-        double xn = x - f / df;
-        if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-        if (fabs(xn - x) <= 1e-15 || hi - lo <= 1e-15) {
-            x = xn;
-            break;
-        }
-        x = xn;
-    }
-    return x;
+    return first_root(P, iters);
 }
 
 // Step (C) after the crossing time is known: y = psi(tau) is in a shared-memory
@@ -795,10 +810,524 @@ __device__ void run_trajectory(const KernelArgs &a, const Group<G> &g, const int
     }
 }
 
+// ---------------------------------------------------------------------------
+// Dormand-Prince 5(4) in Krylov form, for a constant operator
+// ---------------------------------------------------------------------------
+//
+// For dpsi/dt = M psi with a constant M every stage of an explicit Runge-Kutta
+// step is a polynomial in hM applied to psi: h K_j = sum_k kappa_jk (hM)^k psi with
+// kappa_j1 = 1 and kappa_j,k+1 = sum_l a_jl kappa_lk.  Hence the 5th-order solution
+// is sum_{k<=6} beta_k (hM)^k psi (beta_k = sum_j b_j kappa_jk, beta_0 = 1), the
+// local error estimate sum_{k=5..7} gamma_k (hM)^k psi (gamma_k = sum_j (b_j -
+// bhat_j) kappa_jk; gamma_0..4 vanish because both weights are exact to 4th
+// order), and the continuous extension psi + sum_m theta^m sum_k Q_mk (hM)^k psi
+// (Q_mk = sum_j W_jm kappa_jk).  A step therefore needs the Krylov vectors
+// M^k psi, k <= 7 -- the same six products per step as the stage form, the first
+// of them left over from the previous step -- and no stage combinations; the
+// error estimate is a sum of three terms of the size of the error, with none of
+// the stage form's cancellation, so FP32 forms it; and after a rejected step
+// the vectors stay valid, only the coefficients change with h.  It is the same
+// method with the same step sequence as the stage form, up to rounding.
+//
+// To keep the vectors in range whatever the size of M, the kernel holds
+// wt_k = (2^-e M)^k psi with 2^e above ||M|| (a power of two, so the scaling is
+// exact) and folds (h 2^e)^k into the coefficients.
+
+// The Krylov-form coefficients in the policy's arithmetic, per CTA.
+template <class Ar>
+struct KCoefs {
+    typename Ar::coef beta[7];  // 5th-order solution: beta_k, k = 0..6
+    typename Ar::coef Q[5][8];  // continuous extension: Q[m - 1][k], theta^m, m = 1..5, k = 0..7
+    float gam[3];               // error estimate: gamma_5, gamma_6, gamma_7
+};
+
+// kappa, beta, gamma and Q from the Dormand-Prince tableau (FP64; one thread per CTA)
+template <class Ar>
+__device__ __noinline__ void krylov_coefs(KCoefs<Ar> *K)
+{
+    double kap[7][8];
+#pragma unroll 1
+    for (int j = 0; j < 7; ++j) {
+        for (int k = 0; k < 8; ++k) kap[j][k] = 0.0;
+        kap[j][1] = 1.0;
+        for (int k = 1; k < 7; ++k) {
+            double v = 0.0;
+            for (int l = 0; l < j; ++l) v += DP5::a(j, l) * kap[l][k];
+            kap[j][k + 1] = v;
+        }
+    }
+    for (int k = 0; k < 7; ++k) {
+        double b = k == 0 ? 1.0 : 0.0;
+        for (int j = 0; j < 7; ++j) b += DP5::b(j) * kap[j][k];
+        K->beta[k] = Ar::coef_of(b);
+    }
+    for (int k = 5; k < 8; ++k) {
+        double e = 0.0;
+        for (int j = 0; j < 7; ++j) e += DP5::e(j) * kap[j][k];
+        K->gam[k - 5] = (float)e;
+    }
+    for (int m = 1; m <= 5; ++m)
+        for (int k = 0; k < 8; ++k) {
+            double q = 0.0;
+            for (int j = 0; j < 7; ++j) q += DP5::W(j, m) * kap[j][k];
+            K->Q[m - 1][k] = Ar::coef_of(q);
+        }
+}
+
+// The scalars of the current step size in shared memory, one copy per warp:
+// formed by the warp's lanes in parallel (entry k by lane k mod the warp's share
+// of the group) and read by them, so the step's rolled loops index them without
+// local memory and only a warp-level synchronisation guards them.
+template <class Ar>
+struct KStep {
+    typename Ar::coef hp[8];  // H^k, H = h 2^e
+    typename Ar::coef c[8];   // beta_k H^k, k = 1..6 (5th-order solution and the next first stage)
+    typename Ar::coef d[8];   // rho_k(theta) H^k, k = 1..7 (continuous extension at one theta)
+    float ge[4];              // gamma_k H^k, k = 5..7 (error estimate)
+};
+
+// Slots of the Krylov form: psi, wt_1..wt_7, the candidate and a scratch vector.
+enum KSlot { kKPsi = 0 /* wt_k in slot k, k = 1..7 */, kKYn = 8, kKScr = 9 };
+
+// Lanes that share one KStep copy and the synchronisation among them.
+template <int G>
+__device__ __forceinline__ void kstep_sync(const Group<G> &g)
+{
+    if constexpr (G > 32)
+        __syncwarp();
+    else
+        g.sync();
+}
+template <int G>
+__host__ __device__ constexpr int kstep_lanes() { return G > 32 ? 32 : G; }
+
+// KS->hp, c, ge for step size H (synchronised among the copy's lanes on return)
+template <class Ar, int G>
+__device__ __forceinline__ void krylov_step_coefs(const KCoefs<Ar> &KC, KStep<Ar> *KS, const Group<G> &g, double H)
+{
+    using coef = typename Ar::coef;
+    constexpr int W = kstep_lanes<G>();
+    kstep_sync(g);  // the previous step's readers are done
+    const coef h1 = Ar::coef_of(H);
+#pragma unroll 1
+    for (int k = g.gl % W; k < 8; k += W) {
+        coef p = Ar::coef_of(1.0);
+#pragma unroll 1
+        for (int i = 0; i < k; ++i) p = Ar::cmul(p, h1);
+        KS->hp[k] = p;
+        if (k >= 1 && k <= 6) KS->c[k] = Ar::cmul(KC.beta[k], p);
+        if (k >= 5) KS->ge[k - 5] = KC.gam[k - 5] * Ar::coef32(p);
+    }
+    kstep_sync(g);
+}
+
+// KS->d for the continuous extension at theta (uses KS->hp; synchronised on return)
+template <class Ar, int G>
+__device__ __forceinline__ void krylov_dense_coefs(const KCoefs<Ar> &KC, KStep<Ar> *KS, const Group<G> &g, double th)
+{
+    using coef = typename Ar::coef;
+    constexpr int W = kstep_lanes<G>();
+    kstep_sync(g);
+    const coef tc = Ar::coef_of(th);
+#pragma unroll 1
+    for (int k = 1 + g.gl % W; k < 8; k += W) {
+        coef p = KC.Q[4][k];
+#pragma unroll 1
+        for (int m = 3; m >= 0; --m) p = Ar::cadd(Ar::cmul(p, tc), KC.Q[m][k]);
+        KS->d[k] = Ar::cmul(Ar::cmul(p, tc), KS->hp[k]);
+    }
+    kstep_sync(g);
+}
+
+// body(r) for the lane's rows r < R: rolled for single-warp groups (a small hot
+// loop), unrolled for multi-warp groups, whose threads then advance their R rows
+// as independent chains
+template <int G, int R, class F>
+__device__ __forceinline__ void krylov_rows(F &&body)
+{
+    if constexpr (G > 32) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) body(r);
+    } else {
+#pragma unroll 1
+        for (int r = 0; r < R; ++r) body(r);
+    }
+}
+
+// |e|^2 / sc^2 of one row in FP32, e = (ere, eim) formed directly
+template <class Ar>
+__device__ __forceinline__ float krylov_err_term(float ere, float eim, typename Ar::cplx y0, typename Ar::cplx y1,
+                                                 double rtol, double atol)
+{
+    const float ay2 = Ar::re32(y0) * Ar::re32(y0) + Ar::im32(y0) * Ar::im32(y0);
+    const float an2 = Ar::re32(y1) * Ar::re32(y1) + Ar::im32(y1) * Ar::im32(y1);
+    const float sc = (float)atol + (float)rtol * sqrtf(ay2 > an2 ? ay2 : an2);
+    return (ere * ere + eim * eim) / (sc * sc);
+}
+
+// dst = psi + sum_k d_k wt_k on the lane's rows (the continuous extension at the
+// theta of KS->d); the caller synchronises before dst is gathered
+template <class Ar, int G, int R>
+__device__ __noinline__ void krylov_dense(const KStep<Ar> *KS, const Lanes<Ar, G, R> &L, typename Ar::cplx *dst)
+{
+    krylov_rows<G, R>([&](int r) {
+        const int row = L.gl + G * r;
+        if (row < L.n) {
+            typename Ar::acc acc = Ar::acc_of(L.slot(kKPsi)[row]);
+#pragma unroll 1
+            for (int k = 1; k < 8; ++k) Ar::axpy(acc, KS->d[k], L.slot(k)[row]);
+            dst[row] = Ar::get(acc);
+        }
+    });
+}
+
+// First theta in (0, 1] with ||y(theta)||^2 = r on the Krylov-form continuous
+// extension: y(theta) = sum_m theta^m u_m, u_0 = psi, u_m = sum_k Q[m - 1][k] H^k wt_k.
+template <class Ar, int G, int R>
+__device__ __noinline__ double krylov_crossing(const KCoefs<Ar> &KC, const KStep<Ar> *KS, const Lanes<Ar, G, R> &L,
+                                               const Group<G> &g, double r, int &iters)
+{
+    using cplx = typename Ar::cplx;
+    typename Ar::red gram[21];
+#pragma unroll
+    for (int i = 0; i < 21; ++i) gram[i] = Ar::rzero();
+#pragma unroll 1
+    for (int rr = 0; rr < R; ++rr) {
+        const int row = L.gl + G * rr;
+        if (row >= L.n) continue;
+        cplx u[6];
+        u[0] = L.slot(kKPsi)[row];
+#pragma unroll
+        for (int m = 1; m <= 5; ++m) {
+            typename Ar::acc acc = Ar::zero();
+#pragma unroll 1
+            for (int k = 1; k < 8; ++k) Ar::axpy(acc, Ar::cmul(KC.Q[m - 1][k], KS->hp[k]), L.slot(k)[row]);
+            u[m] = Ar::get(acc);
+        }
+        int i = 0;
+#pragma unroll
+        for (int m = 0; m < 6; ++m)
+#pragma unroll
+            for (int m2 = m; m2 < 6; ++m2, ++i) gram[i] = Ar::radd(gram[i], Ar::dot_re(u[m], u[m2]));
+    }
+    double P[11];
+#pragma unroll
+    for (int s = 0; s < 11; ++s) P[s] = 0.0;
+    {
+        int i = 0;
+#pragma unroll
+        for (int m = 0; m < 6; ++m)
+#pragma unroll
+            for (int m2 = m; m2 < 6; ++m2, ++i) {
+                const double v = Ar::rval(Ar::rsum(g, gram[i]));
+                P[m + m2] += (m == m2) ? v : 2.0 * v;
+            }
+    }
+    P[0] -= r;
+    return first_root(P, iters);
+}
+
+// out[row] = 2^-e (M x)[row] on the lane's rows (x synchronised)
+template <class Ar, int G, int R>
+__device__ __forceinline__ void krylov_product(const CsrView<Ar> &M, const typename Ar::cplx *x,
+                                               typename Ar::cplx *out, int gl, int n, float down)
+{
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
+        const typename Ar::cplx v = spmv_row<Ar, G>(M, x, gl, r);
+        const int row = gl + G * r;
+        if (row < n) out[row] = Ar::mul_pow2(v, down);
+    }
+}
+
+// The starting step (Hairer, Norsett & Wanner, Sec. II.4) from psi with
+// f0 = M psi, in FP64 scalars; wt_1 = 2^-e M psi is left in slot 1 (synchronised).
+template <class Ar, int G, int R>
+__device__ __noinline__ double krylov_start(const KernelArgs &a, const Group<G> &g, const CsrView<Ar> &M,
+                                            const Lanes<Ar, G, R> &L, double span, float down, double up)
+{
+    using cplx = typename Ar::cplx;
+    const int n = a.n, gl = g.gl;
+    const double rtol = a.rtol, atol = a.atol;
+    cplx *psi = L.slot(kKPsi), *w1 = L.slot(1), *scr = L.slot(kKScr), *f1 = L.slot(kKYn);
+    krylov_product<Ar, G, R>(M, psi, w1, gl, n, down);
+    double d0 = 0.0, d1 = 0.0;
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
+        const int row = gl + G * r;
+        if (row < n) {
+            const double yr = Ar::re(psi[row]), yi = Ar::im(psi[row]);
+            const double fr = up * Ar::re(w1[row]), fi = up * Ar::im(w1[row]);
+            const double sc = atol + rtol * sqrt(yr * yr + yi * yi);
+            d0 += (yr * yr + yi * yi) / (sc * sc);
+            d1 += (fr * fr + fi * fi) / (sc * sc);
+        }
+    }
+    d0 = sqrt(g.sum(d0) / n);
+    d1 = sqrt(g.sum(d1) / n);
+    double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
+    if (h0 > span) h0 = span;
+    const typename Ar::coef h0c = Ar::coef_of(h0 * up);
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
+        const int row = gl + G * r;
+        if (row < n) {
+            typename Ar::acc acc = Ar::acc_of(psi[row]);
+            Ar::axpy(acc, h0c, w1[row]);
+            scr[row] = Ar::get(acc);
+        }
+    }
+    g.sync();
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
+        const cplx v = spmv_row<Ar, G>(M, scr, gl, r);
+        const int row = gl + G * r;
+        if (row < n) f1[row] = v;
+    }
+    double d2 = 0.0;
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
+        const int row = gl + G * r;
+        if (row < n) {
+            const double yr = Ar::re(psi[row]), yi = Ar::im(psi[row]);
+            const double sc = atol + rtol * sqrt(yr * yr + yi * yi);
+            const double dre = Ar::re(f1[row]) - up * Ar::re(w1[row]);
+            const double dim = Ar::im(f1[row]) - up * Ar::im(w1[row]);
+            d2 += (dre * dre + dim * dim) / (sc * sc);
+        }
+    }
+    d2 = sqrt(g.sum(d2) / n) / h0;
+    g.sync();
+    const double dm = d1 > d2 ? d1 : d2;
+    const double h1 = (dm <= 1e-15) ? fmax(1e-6, h0 * 1e-3) : pow(0.01 / dm, 0.2);
+    double h = 100.0 * h0 < h1 ? 100.0 * h0 : h1;
+    if (h > span) h = span;
+    return h;
+}
+
+// Algorithm 1 for one trajectory with the Krylov form of the Dormand-Prince step
+// (the plain double-float and complex64 kernels: constant M, no proposal).  The
+// loops stay rolled and read their coefficients from KS, which keeps the step
+// loop inside the instruction cache.
+template <class Ar, int G, int R>
+__device__ void run_trajectory_krylov(const KernelArgs &a, const Group<G> &g, const int *si,
+                                      const typename Ar::real *sv, const KCoefs<Ar> &KC, KStep<Ar> *KS,
+                                      Lanes<Ar, G, R> &L, long long il)
+{
+    using cplx = typename Ar::cplx;
+    const int n = a.n;
+    const int gl = g.gl;
+    const long long traj = a.traj0 + il;
+    const double t_end = a.t[a.n_t - 1];
+    double *out = a.out + (size_t)il * a.n_t * a.n_obs;
+    const CsrView<Ar> M = csr_view<Ar>(a.op[0], si, sv);
+    const double rtol = a.rtol, atol = a.atol;
+    const float down = __int_as_float((127 - a.krylov_shift) << 23);  // 2^-e
+    const double up = ldexp(1.0, a.krylov_shift);                       // 2^e
+    cplx *psi = L.slot(kKPsi);
+    cplx *yn = L.slot(kKYn);
+    cplx *scr = L.slot(kKScr);
+
+    int status = 0;
+    long long attempts = 0;
+    unsigned long long n_acc = 0, n_rej = 0, n_rhs = 0, n_jump = 0;
+    int root_iters = 0;
+
+    // (A)
+    const cplx *psi0 = static_cast<const cplx *>(a.psi0);
+#pragma unroll 1
+    for (int r = 0; r < R; ++r) {
+        const int row = gl + G * r;
+        if (row < n) psi[row] = psi0[row];
+    }
+    g.sync();
+    long long k = 0;
+    double rk, ck;
+    jump_draws(a.seed, traj, k, rk, ck);
+    double t = a.t[0];
+    record_outputs<Ar, G, R>(a, g, si, sv, psi, 0, out, nullptr);
+    int j = 1;
+    double h = krylov_start<Ar, G, R>(a, g, M, L, t_end - t, down, up);
+    n_rhs += 2;
+
+    bool rejected_before = false;
+    int kfrom = 2;  // wt_kfrom..wt_7 still to be formed for the current psi (8: none)
+    while (j < a.n_t) {
+        if (t_end - t <= 4.0 * 2.220446049250313e-16 * fabs(t_end)) {
+            g.sync();
+            for (; j < a.n_t; ++j) record_outputs<Ar, G, R>(a, g, si, sv, psi, j, out, nullptr);
+            break;
+        }
+        if (attempts >= a.max_steps) {
+            status = 4;
+            break;
+        }
+        bool last = false;
+        if (t + 1.01 * h >= t_end) {
+            h = t_end - t;
+            last = true;
+        }
+        if (h < 1e-14 * fmax(1.0, fabs(t))) {
+            status = 5;
+            break;
+        }
+        // (B): the Krylov vectors of psi; after a rejection they are still valid
+#pragma unroll 1
+        for (int q = kfrom; q < 8; ++q) {
+            g.sync();  // wt_{q-1} complete in every lane
+            krylov_product<Ar, G, R>(M, L.slot(q - 1), L.slot(q), gl, n, down);
+        }
+        n_rhs += 8 - kfrom;
+        kfrom = 8;
+        ++attempts;
+        krylov_step_coefs<Ar, G>(KC, KS, g, h * up);
+
+        typename Ar::errt esum = 0;
+        typename Ar::red nr = Ar::rzero();
+        krylov_rows<G, R>([&](int r) {
+            const int row = gl + G * r;
+            if (row < n) {
+                const cplx y0 = psi[row];
+                typename Ar::acc acc = Ar::acc_of(y0);
+#pragma unroll 1
+                for (int q = 1; q < 7; ++q) Ar::axpy(acc, KS->c[q], L.slot(q)[row]);
+                const cplx y1 = Ar::get(acc);
+                yn[row] = y1;
+                const cplx w5 = L.slot(5)[row], w6 = L.slot(6)[row], w7 = L.slot(7)[row];
+                const float ere = fmaf(KS->ge[0], Ar::re32(w5),
+                                       fmaf(KS->ge[1], Ar::re32(w6), KS->ge[2] * Ar::re32(w7)));
+                const float eim = fmaf(KS->ge[0], Ar::im32(w5),
+                                       fmaf(KS->ge[1], Ar::im32(w6), KS->ge[2] * Ar::im32(w7)));
+                esum += krylov_err_term<Ar>(ere, eim, y0, y1, rtol, atol);
+                nr = Ar::radd(nr, Ar::abs2(y1));
+            }
+        });
+        const double err = Ar::err_final(Ar::err_sum(g, esum), n);
+
+        if (!(err <= 1.0)) {
+            if (!isfinite(err)) {
+                status = 6;
+                break;
+            }
+            double fac = Ar::controller(err);
+            if (fac < kFacMin) fac = kFacMin;
+            h *= fac;
+            rejected_before = true;
+            ++n_rej;
+            continue;
+        }
+        ++n_acc;
+        const double t_new = last ? t_end : t + h;
+        const double nn = Ar::rval(Ar::rsum(g, nr));
+
+        if (nn < rk) {
+            // (C): the norm reached r inside this step
+            const double th = krylov_crossing<Ar, G, R>(KC, KS, L, g, rk, root_iters);
+            double tau = t + th * h;
+            if (tau > t_new) tau = t_new;
+            for (; j < a.n_t && a.t[j] <= tau; ++j) {
+                double thj = (a.t[j] - t) / h;
+                if (thj > 1.0) thj = 1.0;
+                krylov_dense_coefs<Ar, G>(KC, KS, g, thj);
+                krylov_dense<Ar, G, R>(KS, L, scr);
+                g.sync();
+                record_outputs<Ar, G, R>(a, g, si, sv, scr, j, out, nullptr);
+            }
+            krylov_dense_coefs<Ar, G>(KC, KS, g, th);
+            krylov_dense<Ar, G, R>(KS, L, scr);
+            g.sync();
+            // the candidate is dead after a crossing: its slot serves as scratch
+            const int ch = apply_jump<Ar, G, R>(a, g, si, sv, psi, yn, scr, ck);
+            if (ch < 0) {
+                status = 7;
+                break;
+            }
+            if (gl == 0 && (long long)n_jump < a.max_jumps) {
+                a.jump_t[(size_t)il * a.max_jumps + n_jump] = tau;
+                a.jump_ch[(size_t)il * a.max_jumps + n_jump] = ch;
+            }
+            ++n_jump;
+            // (D): the Krylov vectors of the new psi, from wt_1, at the next attempt
+            ++k;
+            jump_draws(a.seed, traj, k, rk, ck);
+            t = tau;
+            kfrom = 1;
+            rejected_before = false;
+            continue;
+        }
+
+        for (; j < a.n_t && a.t[j] <= t_new; ++j) {
+            double thj = (a.t[j] - t) / h;
+            if (thj > 1.0) thj = 1.0;
+            krylov_dense_coefs<Ar, G>(KC, KS, g, thj);
+            krylov_dense<Ar, G, R>(KS, L, scr);
+            g.sync();
+            record_outputs<Ar, G, R>(a, g, si, sv, scr, j, out, nullptr);
+        }
+        double fac = (err == 0.0) ? kFacMax : Ar::controller(err);
+        if (fac > kFacMax) fac = kFacMax;
+        if (fac < kFacMin) fac = kFacMin;
+        if (rejected_before && fac > 1.0) fac = 1.0;
+        rejected_before = false;
+        t = t_new;
+        // first same as last: wt_1 <- 2^-e M ynew = wt_1 + sum_{k=1..6} c_k wt_{k+1}; psi <- ynew
+        krylov_rows<G, R>([&](int r) {
+            const int row = gl + G * r;
+            if (row < n) {
+                typename Ar::acc acc = Ar::acc_of(L.slot(1)[row]);
+#pragma unroll 1
+                for (int q = 1; q < 7; ++q) Ar::axpy(acc, KS->c[q], L.slot(q + 1)[row]);
+                L.slot(1)[row] = Ar::get(acc);
+                psi[row] = yn[row];
+            }
+        });
+        kfrom = 2;
+        h *= fac;
+    }
+
+    if (gl == 0) {
+        if (status != 0) {
+            for (; j < a.n_t; ++j)
+                for (int q = 0; q < a.n_obs; ++q)
+                    out[(size_t)j * a.n_obs + q] = __longlong_as_double(0x7ff8000000000000LL);
+            atomicCAS(a.first_error, 0, status);
+            atomicAdd(&a.counters[kFailed], 1ULL);
+        }
+        if (a.max_jumps > 0) a.n_jumps[il] = (int)n_jump;
+        atomicAdd(&a.counters[kAccepted], n_acc);
+        atomicAdd(&a.counters[kRejected], n_rej);
+        atomicAdd(&a.counters[kRhs], n_rhs);
+        atomicAdd(&a.counters[kJumps], n_jump);
+        atomicAdd(&a.counters[kRootIters], (unsigned long long)root_iters);
+    }
+}
+
 // Threads per CTA for a group size: 4 warps for single-warp groups, 8 warps (one
 // to four groups) for multi-warp groups.
 template <int G>
 __host__ __device__ constexpr int block_for_group() { return G <= 32 ? 128 : 256; }
+
+// The step form of an instantiation: the Krylov form (constant operator) for the
+// plain double-float and complex64 kernels; the stage form for complex128 (the
+// plain FP64 path, written as the oracle writes it) and for every kernel with a
+// time-dependent term or the learned proposal.
+template <class Ar, int FEAT>
+__host__ __device__ constexpr bool use_krylov() { return FEAT == 0 && Ar::kId != ArF64::kId; }
+
+// CTA size and the CTAs per SM the register budget is set for.  The single-warp
+// Krylov kernels run ten warps per CTA and two CTAs per SM where the ten slots
+// of that many groups stay near 100 KB (R x complex size <= 32 bytes): one
+// operator copy per ten warps instead of per four leaves room for 20 resident
+// warps (at most 102 registers) instead of 16, which hides more of the step's
+// latency.
+template <class Ar, int G, int R, int FEAT>
+__host__ __device__ constexpr int trajectory_block()
+{
+    return (G <= 32 && use_krylov<Ar, FEAT>() && R * sizeof(typename Ar::cplx) <= 32) ? 10 * 32
+                                                                                     : block_for_group<G>();
+}
+template <int G, int BLOCK>
+__host__ __device__ constexpr int trajectory_min_ctas() { return G > 32 ? 1 : (BLOCK > 128 ? 2 : 4); }
 
 // Operators are staged into shared memory for single-warp groups (small N); the
 // operators of multi-warp groups (N > 64) are read from global memory, where
@@ -807,7 +1336,7 @@ template <int G>
 __host__ __device__ constexpr bool ops_in_shared() { return G <= 32; }
 
 template <class Ar, int G, int R, int BLOCK, int FEAT>
-__global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 1)) mcwf_kernel(const __grid_constant__ KernelArgs a)
+__global__ void __launch_bounds__(BLOCK, (trajectory_min_ctas<G, BLOCK>())) mcwf_kernel(const __grid_constant__ KernelArgs a)
 {
     using cplx = typename Ar::cplx;
     using real = typename Ar::real;
@@ -826,14 +1355,21 @@ __global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 1)) mcwf_kernel(const __
         si = a.ints;
         sv = static_cast<const real *>(a.vals);
     }
+    // the plain double-float and complex64 kernels take the Krylov form of the step
+    constexpr bool KRYLOV = use_krylov<Ar, FEAT>();
     Coefs<Ar> *C = reinterpret_cast<Coefs<Ar> *>(smem + a.smem_coef_offset);
-    for (int i = threadIdx.x; i < 42 + 7 + 35; i += BLOCK) {
-        if (i < 42)
-            C->a[i / 6][i % 6] = Ar::coef_of(DP5::a(i / 6, i % 6));
-        else if (i < 49)
-            C->e[i - 42] = Ar::coef_of(DP5::e(i - 42));
-        else
-            C->W[(i - 49) / 5][(i - 49) % 5] = Ar::coef_of(DP5::W((i - 49) / 5, (i - 49) % 5 + 1));
+    KCoefs<Ar> *KC = reinterpret_cast<KCoefs<Ar> *>(smem + a.smem_coef_offset);
+    if constexpr (KRYLOV) {
+        if (threadIdx.x == 0) krylov_coefs<Ar>(KC);
+    } else {
+        for (int i = threadIdx.x; i < 42 + 7 + 35; i += BLOCK) {
+            if (i < 42)
+                C->a[i / 6][i % 6] = Ar::coef_of(DP5::a(i / 6, i % 6));
+            else if (i < 49)
+                C->e[i - 42] = Ar::coef_of(DP5::e(i - 42));
+            else
+                C->W[(i - 49) / 5][(i - 49) % 5] = Ar::coef_of(DP5::W((i - 49) / 5, (i - 49) % 5 + 1));
+        }
     }
     __syncthreads();
 
@@ -843,13 +1379,17 @@ __global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 1)) mcwf_kernel(const __
     unsigned char *pbase = smem + a.smem_mlp_offset + (size_t)(threadIdx.x / G) * kPropStride;
     constexpr bool PROP = (FEAT & kFeatProposal) != 0;
     float *hscratch = PROP ? reinterpret_cast<float *>(pbase) : nullptr;
+    KStep<Ar> *KS = reinterpret_cast<KStep<Ar> *>(smem + a.smem_mlp_offset) + threadIdx.x / kstep_lanes<G>();
     PropState *P = PROP ? reinterpret_cast<PropState *>(pbase + kMlpHidden * sizeof(float)) : nullptr;
     for (;;) {
         unsigned long long i = 0;
         if (g.gl == 0) i = atomicAdd(a.queue, 1ULL);
         i = g.bcast0(i);
         if ((long long)i >= a.ntraj) break;
-        run_trajectory<Ar, G, R, FEAT>(a, g, si, sv, *C, L, hscratch, P, (long long)i);
+        if constexpr (KRYLOV)
+            run_trajectory_krylov<Ar, G, R>(a, g, si, sv, *KC, KS, L, (long long)i);
+        else
+            run_trajectory<Ar, G, R, FEAT>(a, g, si, sv, *C, L, hscratch, P, (long long)i);
     }
 }
 
@@ -858,15 +1398,16 @@ template <class Ar, int G, int R, int FEAT = 0>
 cudaError_t launch_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInfo *info)
 {
     using cplx = typename Ar::cplx;
-    constexpr int BLOCK = block_for_group<G>();
+    constexpr int BLOCK = trajectory_block<Ar, G, R, FEAT>();
     constexpr int GROUPS = BLOCK / G;
     KernelArgs a = a0;
     auto al16 = [](size_t x) { return (x + 15) & ~size_t(15); };
     const size_t ib = ops_in_shared<G>() ? al16((size_t)a.n_ints * sizeof(int)) : 0;
     const size_t vb = ops_in_shared<G>() ? al16((size_t)a.n_vals * sizeof(typename Ar::real)) : 0;
-    const size_t cb = al16(sizeof(Coefs<Ar>));
+    const size_t cb = al16(sizeof(Coefs<Ar>) > sizeof(KCoefs<Ar>) ? sizeof(Coefs<Ar>) : sizeof(KCoefs<Ar>));
     const size_t sb = al16((size_t)GROUPS * (Group<G>::kWarps + 1) * 8);
-    const size_t mb = (FEAT & kFeatProposal) ? (size_t)GROUPS * kPropStride : 0;
+    const size_t mb = (FEAT & kFeatProposal) ? (size_t)GROUPS * kPropStride
+                      : use_krylov<Ar, FEAT>() ? al16((size_t)(BLOCK / kstep_lanes<G>()) * sizeof(KStep<Ar>)) : 0;
     a.smem_vals_offset = (int)ib;
     a.smem_coef_offset = (int)(ib + vb);
     a.smem_scratch_offset = (int)(ib + vb + cb);

@@ -74,6 +74,7 @@ struct qtm_ctx {
     DevBuf d_ints, d_vals, d_t, d_psi0, d_queue, d_counters, d_first_error;
     DevBuf d_out, d_partial, d_moments, d_scale, d_njumps, d_jump_t, d_jump_ch;
     std::vector<int> scale_exp;  // per observable: values are bounded by 2^(E - 1) (moments.h)
+    int krylov_shift = 0;        // 2^krylov_shift > ||M|| (Krylov form of the Dormand-Prince step)
     // learned jump-time proposal
     DevBuf d_rec, d_mlp, d_X, d_T, d_gpart, d_lpart, d_grad, d_loss, d_m, d_v;
     int rec_stride = 0, rec_max = 0;
@@ -769,6 +770,11 @@ qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
     ctx->Cops = C;
     ctx->Aops = A;
     for (int i = 0; i < p->n_obs; ++i) ctx->scale_exp.push_back(observable_scale(A[i]));
+    {
+        const double nu = op_norm_bound(ctx->M);  // >= ||M||_2
+        const int e = nu > 0.0 ? std::ilogb(nu) + 1 : 0;
+        ctx->krylov_shift = std::max(-100, std::min(100, e));
+    }
     // the tensor-core engine's control warps use one lane per row group of 32
     repack(ctx, p->precision == QTM_PREC_BF16X6 ? qtm::Layout{32, qtm::tc_padded_dim(n) / 32}
                                                 : qtm::layout_for_dim(n));
@@ -778,8 +784,13 @@ qtm_status qtm_create(const qtm_problem *p, void *cuda_stream, qtm_ctx **out)
         // ones) go to the 64-lane layout, whose kernels read them from L2
         const size_t real_b = p->precision == QTM_PREC_C64 ? 4 : 8;
         const size_t cplx_b = p->precision == QTM_PREC_C64 ? 8 : 16;
+        // threads per CTA of the plain kernel (trajectory_block): 320 for the
+        // double-float and complex64 kernels with R x complex size <= 32 bytes
+        const bool big = (p->precision == QTM_PREC_DF64 || p->precision == QTM_PREC_C64) &&
+                         ctx->layout.R * cplx_b <= 32;
+        const size_t groups = (big ? 320 : 128) / ctx->layout.G;
         const size_t need = ctx->ints.size() * 4 + ctx->reals.size() * real_b +
-                            4 * 10 * (size_t)ctx->layout.G * ctx->layout.R * cplx_b + 4096;
+                            groups * 10 * (size_t)ctx->layout.G * ctx->layout.R * cplx_b + 4096;
         if (need > 220 * 1024) repack(ctx, qtm::Layout{64, 2});
     }
 
@@ -922,6 +933,7 @@ static qtm_status enqueue_run(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64
         a.rec = (float *)ctx->d_rec.p;
         a.mlp = ctx->mlp_on ? (const float *)ctx->d_mlp.p : nullptr;
         a.prop_margin = ctx->prop_margin;
+        a.krylov_shift = ctx->krylov_shift;
         const bool prop = a.rec_stride > 0 || a.mlp != nullptr;
         if (ctx->precision == QTM_PREC_BF16X6) {
             if (prop) return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_run: no learned proposal on the tensor-core path");
@@ -946,17 +958,20 @@ static qtm_status enqueue_run(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64
                         "qtm_run: the learned proposal needs complex128 or double-float and dimension <= 64");
         if (prop && a.n_drive > 0)
             return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_run: the learned proposal takes a constant Hamiltonian");
-        if (ctx->method == QTM_METHOD_EXPONENTIAL && (prop || a.n_drive > 0))
-            return fail(ctx, QTM_ERR_UNSUPPORTED,
-                        "qtm_run: the exponential method takes a constant Hamiltonian and no learned proposal");
+        if (ctx->method == QTM_METHOD_EXPONENTIAL && a.n_drive > 0)
+            return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_run: the exponential method takes a constant Hamiltonian");
         if (ctx->method == QTM_METHOD_EXPONENTIAL) {
             a.expo = ctx->d_expo.p;
             a.expo_levels = ctx->expo_levels;
             a.expo_uniform = ctx->expo_uniform;
             a.expo_delta = ctx->expo_delta;
-            e = ctx->precision == QTM_PREC_DF64  ? qtm::launch_mcwf_df64_expo(a, s, &ctx->info)
-              : ctx->precision == QTM_PREC_C64   ? qtm::launch_mcwf_c64_expo(a, s, &ctx->info)
-                                                 : qtm::launch_mcwf_c128_expo(a, s, &ctx->info);
+            if (prop)
+                e = ctx->precision == QTM_PREC_DF64 ? qtm::launch_mcwf_df64_expo_prop(a, s, &ctx->info)
+                                                    : qtm::launch_mcwf_c128_expo_prop(a, s, &ctx->info);
+            else
+                e = ctx->precision == QTM_PREC_DF64  ? qtm::launch_mcwf_df64_expo(a, s, &ctx->info)
+                  : ctx->precision == QTM_PREC_C64   ? qtm::launch_mcwf_c64_expo(a, s, &ctx->info)
+                                                     : qtm::launch_mcwf_c128_expo(a, s, &ctx->info);
         } else if (a.n_drive > 0)
             e = ctx->precision == QTM_PREC_DF64  ? qtm::launch_mcwf_df64_drive(a, s, &ctx->info)
               : ctx->precision == QTM_PREC_C64   ? qtm::launch_mcwf_c64_drive(a, s, &ctx->info)
@@ -1347,6 +1362,7 @@ qtm_status qtm_stats(qtm_ctx *ctx, qtm_stats_t *out)
     out->jumps = (int64_t)c[qtm::kJumps];
     out->root_iters = (int64_t)c[qtm::kRootIters];
     out->failed = (int64_t)c[qtm::kFailed];
+    out->proposal_misses = (int64_t)c[qtm::kPropMiss];
     out->first_error = (int32_t)run_status;
     out->kernel_group = ctx->info.group;
     out->kernel_rows = ctx->info.rows;

@@ -106,9 +106,12 @@ struct KernelArgs {
     const void *expo;
     int expo_levels, expo_uniform;
     double expo_delta;
+    // Krylov form of the Dormand-Prince step: 2^krylov_shift >= ||M|| (the
+    // Krylov vectors are kept as (2^-krylov_shift M)^k psi)
+    int krylov_shift;
 };
 
-enum CounterIndex { kAccepted = 0, kRejected, kRhs, kJumps, kRootIters, kFailed, kNumCounters };
+enum CounterIndex { kAccepted = 0, kRejected, kRhs, kJumps, kRootIters, kFailed, kPropMiss, kNumCounters };
 
 struct LaunchInfo {
     int group, rows, grid, block;
@@ -140,6 +143,9 @@ cudaError_t launch_mcwf_c64_drive(const KernelArgs &args, cudaStream_t stream, L
 cudaError_t launch_mcwf_c128_expo(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
 cudaError_t launch_mcwf_df64_expo(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
 cudaError_t launch_mcwf_c64_expo(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+// The exponential-propagation kernel with the learned proposal (single-warp layouts only).
+cudaError_t launch_mcwf_c128_expo_prop(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+cudaError_t launch_mcwf_df64_expo_prop(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
 constexpr int kMaxDimExpo = 256;
 inline cudaError_t launch_mcwf_c128(const KernelArgs &a, cudaStream_t s, LaunchInfo *i)
 {

@@ -34,8 +34,9 @@ TC = Q.QTM_PREC_BF16X6
 def test_product_matches_fp64(orc, name, kw, n_vec, capsys):
     """M y through the tcgen05 BF16x6 product, over 1 vector and over a ragged 300
     (three tiles): FP32-class -- RMS error within 32x that of an FP32 BLAS product
-    of the same inputs -- and no component off by more than 2^-16 of
-    sum_k |M_ik| |y_k|.  The split drops terms of relative size 2^-24; what
+    of the same inputs -- and no component off by more than 2^-18 of
+    sum_k |M_ik| |y_k| (measured: at most 2^-19.8 over these cases).  The split
+    drops terms of relative size 2^-24; what
     remains is the tensor cores' FP32 accumulation, which truncates the aligned
     partial sums instead of rounding them, so its error grows with the length of
     the sum (measured: 5.5x the RMS error of round-to-nearest FP32 at K = 128,
@@ -59,7 +60,7 @@ def test_product_matches_fp64(orc, name, kw, n_vec, capsys):
     worst = float((err / np.where(scale > 0, scale, 1.0)).max())
     with capsys.disabled():
         print(f"\n{name} {kw} n_vec={n_vec}: max |error| / sum|M||y| = 2^{np.log2(max(worst, 1e-300)):.1f}")
-    assert np.all(err <= scale * 2.0 ** -16)
+    assert np.all(err <= scale * 2.0 ** -18)
 
 
 def test_rhs_batch_needs_the_tensor_core_precision():

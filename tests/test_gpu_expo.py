@@ -173,9 +173,6 @@ def test_expo_argument_errors():
     with pytest.raises(Q.QtmError) as ei:
         Q.qtm_set_drive(ctx, [(S.kron(S.eye(5), S.sigma_z()), 1.0, 1.0, 0.0)])
     assert ei.value.status == Q.QTM_ERR_UNSUPPORTED
-    with pytest.raises(Q.QtmError) as ei:
-        Q.qtm_proposal_collect(ctx, 8, 1)
-    assert ei.value.status == Q.QTM_ERR_UNSUPPORTED
     Q.qtm_destroy(ctx)
     drv = S.driven_dephasing_qubit(ntraj=4)
     ctx = Q.qtm_create(drv)
