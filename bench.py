@@ -958,8 +958,10 @@ def learned_proposal(Q, torch, stream, world, rank, dist, ntraj=200000):
                    "steps": (st["accepted"] + st["rejected"]) / count, "jumps": st["jumps"] / count}
     Q.qtm_destroy(ctx)
     off, on = res[False], res[True]
+    expo = _learned_proposal_expo(Q, torch, stream, world, dist, prob, first, count, ntraj)
     return {"workload": f"damped driven Jaynes-Cummings (N=60), {world * ntraj} trajectories (seed 1); "
                         f"network trained on {npairs} pairs from 12,000 trajectories (seed 11)",
+            "exponential_method": expo,
             "precision": "df64", "unit": UNIT,
             "value": world * ntraj / (on["ms"] / 1e3), "plain_value": world * ntraj / (off["ms"] / 1e3),
             "steps_per_trajectory": on["steps"], "plain_steps_per_trajectory": off["steps"],
@@ -968,6 +970,53 @@ def learned_proposal(Q, torch, stream, world, rank, dist, ntraj=200000):
             "observable_error_vs_plain": float(np.abs(on["mean"] - off["mean"]).max()),
             "train": {"pairs": npairs, "steps": steps, "batch": 8192, "loss": loss, "loss_rate_estimate": base,
                       "collect_s": t1 - t0, "train_s": t2 - t1},
+            "launches": RUN_LAUNCHES + 3 * steps + 1 + 4 * RUN_LAUNCHES + expo.pop("launches")}
+
+
+def _learned_proposal_expo(Q, torch, stream, world, dist, prob, first, count, ntraj):
+    """The learned proposal inside the exponential method's crossing search, same
+    workload: pairs from the method's own crossings in 12,000 trajectories (seed
+    11), trained on the GPU, then the 200,000 trajectories timed without and with
+    the proposal (double-float).  Products per trajectory (ladder levels, Taylor
+    and channel products), bracket hits, trajectories/s and the ensemble
+    difference are reported."""
+    sid = int(stream.cuda_stream)
+    ctx = Q.qtm_create(prob, stream=sid, precision=Q.QTM_PREC_DF64)
+    Q.qtm_set_method(ctx, Q.QTM_METHOD_EXPONENTIAL)
+    npairs = Q.qtm_proposal_collect(ctx, 12000, 11, stride=1, max_per_traj=96)
+    steps = 2000
+    loss, base = Q.qtm_proposal_train(ctx, steps=steps, batch=8192, lr=2e-3, seed=11)
+    Q.qtm_run_range(ctx, first, min(count, 20000), prob.seed)  # warm-up of both kernels
+    Q.qtm_proposal_enable(ctx, True, 0.05)
+    Q.qtm_run_range(ctx, first, min(count, 20000), prob.seed)
+    res = {}
+    for on in (False, True):
+        Q.qtm_proposal_enable(ctx, on, 0.05)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        Q.qtm_run_range(ctx, first, count, prob.seed)
+        e1.record(stream)
+        e1.synchronize()
+        t = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        st = Q.qtm_stats(ctx)
+        res[on] = {"ms": float(t.item()), "mean": Q.qtm_expect(ctx)[0], "products": st["rhs_evals"] / count,
+                   "jumps": st["jumps"], "misses": st["proposal_misses"]}
+    Q.qtm_destroy(ctx)
+    off, on = res[False], res[True]
+    return {"precision": "df64", "unit": UNIT,
+            "value": world * ntraj / (on["ms"] / 1e3), "plain_value": world * ntraj / (off["ms"] / 1e3),
+            "products_per_trajectory": on["products"], "plain_products_per_trajectory": off["products"],
+            "product_saving": (off["products"] - on["products"]) / off["products"],
+            "bracket_hit_rate": 1.0 - on["misses"] / max(on["jumps"], 1),
+            "jumps_per_trajectory": on["jumps"] / count,
+            "observable_error_vs_plain": float(np.abs(on["mean"] - off["mean"]).max()),
+            "train": {"pairs": npairs, "steps": steps, "batch": 8192, "loss": loss, "loss_rate_estimate": base},
             "launches": RUN_LAUNCHES + 3 * steps + 1 + 4 * RUN_LAUNCHES}
 
 

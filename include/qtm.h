@@ -167,7 +167,8 @@ typedef struct {
 
 typedef struct qtm_ctx qtm_ctx;
 
-/* Device allocator hooks.  alloc returns device memory usable on `stream` or
+/* Device allocator hooks (no counterpart in the paper: device-memory plumbing).
+ * alloc returns device memory usable on `stream` or
  * NULL; free releases it.  Installing NULL hooks restores cudaMallocAsync /
  * cudaFreeAsync.  Contexts keep the hooks that were installed when they were
  * created.  Not thread-safe with concurrent qtm_create calls. */
@@ -192,7 +193,8 @@ qtm_status qtm_run(qtm_ctx *ctx, int64_t ntraj, uint64_t seed);
  * Results equal those of the same ids in a single larger run. */
 qtm_status qtm_run_range(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64_t seed);
 
-/* Runs several ensembles at once: context i runs global trajectory ids
+/* Runs several ensembles at once (the paper runs one system per mpi_main call,
+ * Sec. 3; batching systems of uneven size is this library's): context i runs global trajectory ids
  * first[i] .. first[i]+ntraj[i]-1 (first may be NULL: all zero) keyed by seed.  All runs are captured into one CUDA graph -- each system's
  * persistent kernel and reduction on its own branch -- and launched on the
  * stream of ctxs[0]; the other contexts' streams wait for that launch, so each
@@ -204,7 +206,8 @@ qtm_status qtm_run_range(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64_t se
 qtm_status qtm_run_batch(qtm_ctx *const *ctxs, const int64_t *first, const int64_t *ntraj, int32_t n,
                          uint64_t seed);
 
-/* Times the lane layouts available for the context's dimension (threads per
+/* No counterpart in the paper (GPU lane mapping).  Times the lane layouts
+ * available for the context's dimension (threads per
  * trajectory x state rows per thread, see qtm_stats_t.kernel_group / kernel_rows)
  * on a run of `sample` trajectories keyed by seed, keeps the fastest, and returns
  * it in *group and *rows (either may be NULL).  Results of later runs do not
@@ -212,7 +215,8 @@ qtm_status qtm_run_batch(qtm_ctx *const *ctxs, const int64_t *first, const int64
  * results. */
 qtm_status qtm_autotune(qtm_ctx *ctx, int64_t sample, uint64_t seed, int32_t *group, int32_t *rows);
 
-/* Selects one of the lane layouts qtm_autotune would consider for the context's
+/* No counterpart in the paper (GPU lane mapping).  Selects one of the lane
+ * layouts qtm_autotune would consider for the context's
  * dimension (e.g. a layout found by an earlier qtm_autotune); QTM_ERR_UNSUPPORTED
  * for any other pair.  Synchronises; discards the results of earlier runs. */
 qtm_status qtm_set_layout(qtm_ctx *ctx, int32_t group, int32_t rows);
@@ -326,10 +330,12 @@ qtm_status qtm_ensemble_reduce_static(const double *values_dev, int64_t ntraj, i
                                       double *sum_dev, double *sumsq_dev, double *mean_dev,
                                       double *stderr_dev, void *cuda_stream);
 
-/* Per-trajectory values of the last run, [traj][j][k] (ntraj * n_t * n_obs doubles). */
+/* The per-trajectory values that Sec. 3 averages: Re<psi|A_k|psi>/<psi|psi> of
+ * every trajectory of the last run at every output time, [traj][j][k]
+ * (ntraj * n_t * n_obs doubles). */
 qtm_status qtm_traj_expect(qtm_ctx *ctx, double *out);
 
-/* Jump records of the last run (needs QTM_FLAG_RECORD_JUMPS): n_jumps[ntraj] total
+/* The jumps of Algorithm 1 step (C) in the last run (needs QTM_FLAG_RECORD_JUMPS): n_jumps[ntraj] total
  * jumps per trajectory; jump_t / jump_ch [ntraj][max_jumps_recorded] hold the first
  * max_jumps_recorded jump times and channel indices (unused slots: NaN / -1). */
 qtm_status qtm_jumps(qtm_ctx *ctx, int32_t *n_jumps, double *jump_t, int32_t *jump_ch);
@@ -412,11 +418,12 @@ qtm_status qtm_mlp_loss_grad(const float *params, const float *x, const float *t
  * Algorithm 1 (B), products, jumps (C), root-find iterations. */
 qtm_status qtm_stats(qtm_ctx *ctx, qtm_stats_t *out);
 
-/* Human-readable message of the last error of ctx (or of the last failed
+/* The error level of the paper's zvode_method_for_mc (Sec. 3) as text:
+ * human-readable message of the last error of ctx (or of the last failed
  * qtm_create when ctx is NULL).  Never NULL; valid until the next call. */
 const char *qtm_last_error(const qtm_ctx *ctx);
 
-/* Name of a status code, e.g. "QTM_ERR_ARG". */
+/* Name of a status code, e.g. "QTM_ERR_ARG" (plumbing; no counterpart in the paper). */
 const char *qtm_status_string(qtm_status status);
 
 /* Time-dependent Hamiltonian (Sec. 3: mpi_main accepts an extra function for a
@@ -431,7 +438,8 @@ const char *qtm_status_string(qtm_status status);
  * when the operators no longer fit a kernel (reported by qtm_run). */
 qtm_status qtm_set_drive(qtm_ctx *ctx, int32_t n_terms, const qtm_op *H, const double *coef);
 
-/* Bound (nanoseconds of wall clock) on any single device-side wait of the
+/* No counterpart in the paper (failure detection of the tensor-core engine).
+ * Bound (nanoseconds of wall clock) on any single device-side wait of the
  * tensor-core engine (QTM_PREC_BF16X6: its producer, tensor-core and TMA roles
  * hand tiles to one another through shared-memory barriers).  A wait that runs
  * past it ends the launch: every role winds down, the engine's device state is
@@ -440,7 +448,8 @@ qtm_status qtm_set_drive(qtm_ctx *ctx, int32_t n_terms, const qtm_op *H, const d
  * arithmetics (their kernels have no cross-role waits). */
 qtm_status qtm_set_wait_limit(qtm_ctx *ctx, uint64_t limit_ns);
 
-/* Batched right-hand side: my[v] = M y[v] with M = -i H_eff, for n_vec vectors
+/* The right-hand side of the trajectory equation (Sec. 2.2, Eq.
+ * eqn:effective:hamiltonian) in batch: my[v] = M y[v] with M = -i H_eff, for n_vec vectors
  * y (HOST, [n_vec][dim] complex, interleaved (re, im) doubles; rounded to FP32)
  * through the tensor-core engine's product (QTM_PREC_BF16X6 contexts only;
  * QTM_ERR_UNSUPPORTED otherwise).  my: HOST, [n_vec][dim] complex.  Runs on the
@@ -488,12 +497,14 @@ qtm_status qtm_rhs_batch(qtm_ctx *ctx, int64_t n_vec, const double *y, double *m
  * QTM_ERR_ARG for any other value. */
 qtm_status qtm_set_method(qtm_ctx *ctx, int32_t method);
 
-/* The exponential method's ladder: number of levels L + 1 and the base step
+/* The exponential method's ladder (exp(M delta 2^l), the no-jump evolution of
+ * Sec. 2.2 over powers of two of a base step): number of levels L + 1 and the base step
  * delta (either pointer may be NULL).  QTM_ERR_STATE when the context does not
  * use the exponential method. */
 qtm_status qtm_expo_ladder(const qtm_ctx *ctx, int32_t *levels, double *delta);
 
-/* exp(M dt) for the problem's M = -i H - (1/2) sum_n C_n^dag C_n (only dim, H,
+/* The no-jump propagator of Sec. 2.2: exp(M dt) for the problem's
+ * M = -i H - (1/2) sum_n C_n^dag C_n (only dim, H,
  * n_c and C are read; HOST pointers), dt >= 0, by the same scaling and squaring
  * as the exponential method's ladder.  out: HOST, n x n complex, row-major,
  * interleaved (re, im).  Needs no GPU; the message of an error is available
@@ -520,10 +531,11 @@ enum {
  * events on the same stream. */
 qtm_status qtm_arith_peak_launch(int32_t kind, int64_t iters, void *scratch_dev, void *cuda_stream, double *flop);
 
-/* Releases the context's device memory (after synchronising its stream). NULL is ignored. */
+/* Releases the context's device memory (after synchronising its stream); the end
+ * of mpi_main's run (Sec. 3).  NULL is ignored. */
 void qtm_destroy(qtm_ctx *ctx);
 
-/* Library version string, e.g. "0.1.0 sm_103a". */
+/* Library version string, e.g. "0.1.0 sm_103a" (no counterpart in the paper). */
 const char *qtm_version(void);
 
 #ifdef __cplusplus

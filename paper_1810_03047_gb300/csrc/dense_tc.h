@@ -1,8 +1,9 @@
 // dense_tc.h -- the tensor-core trajectory engine for dense operators (host view).
 //
 // All trajectories of a CTA advance in lock step as the 128 columns of a state
-// block; each Dormand-Prince stage is one product K_s = M Y_s of the real form of
-// the effective operator (2N x 2N) with the block's 128 stage vectors, computed on
+// block; the Dormand-Prince step is taken in its Krylov form, whose six products
+// per attempt wt_{s+1} = 2^-e M wt_s of the real form of the scaled effective
+// operator (2N x 2N) with the block's 128 vectors are computed on
 // the 5th-generation tensor cores (tcgen05) with both operands split into three
 // bf16 terms (M = M0 + M1 + M2, Y = Y0 + Y1 + Y2) and the six products of combined
 // order <= 2 accumulated in FP32 in tensor memory: FP32-accurate products.
@@ -31,7 +32,7 @@ struct DenseCol {
     long long attempts;         // attempted steps
     unsigned long long n_acc, n_rej, n_rhs, n_jump;
     int j;                      // next output index
-    int sel;                    // bit 0: psi in buffer 1 (else 0); bit 1: K_0 in slot 6 (else 0)
+    int sel;                    // bit 0: psi in buffer 1 (else 0)
     int flags;                  // bit 0: previous attempt rejected; bit 1: this step ends at t_end
     int root_iters;
     int round;                  // trajectories this column has taken (static assignment)
@@ -40,9 +41,9 @@ struct DenseCol {
 static_assert(sizeof(DenseCol) == 128, "DenseCol is 128 bytes");
 
 // State vectors per column: psi buffers 0 and 1 (psi and the candidate ynew swap
-// roles on acceptance), then the stage derivatives K_0 .. K_6 (K_0 and K_6 swap
-// roles on acceptance: first same as last).  Each vector holds 2 np floats: the
-// real parts of rows 0..np-1, then the imaginary parts.
+// roles on acceptance), then the Krylov vectors wt_1 .. wt_7 = (2^-e M)^k psi (wt_1
+// is updated in place on acceptance: first same as last).  Each vector holds
+// 2 np floats: the real parts of rows 0..np-1, then the imaginary parts.
 enum DenseVec { kVPsi0 = 0, kVPsi1 = 1, kVK0 = 2, kNumDenseVecs = 9 };
 
 enum DenseMode { kDenseRun = 0, kDenseRhs = 1 };

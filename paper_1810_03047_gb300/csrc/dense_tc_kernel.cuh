@@ -5,12 +5,22 @@
 // One persistent CTA per SM owns 128 trajectory columns and keeps them busy for
 // the whole launch (a finished column takes the next trajectory id from the
 // device counter).  The columns advance in lock step, one Dormand-Prince attempt
-// at a time, each column with its own t and h:
+// at a time, each column with its own t and h.  The step is taken in its Krylov
+// form (mcwf_kernel.cuh, run_trajectory_krylov): with a constant M every stage is
+// a polynomial in hM applied to psi, so an attempt needs the vectors
+// wt_k = (2^-e M)^k psi, k <= 7, and nothing else:
 //
-//   for s = 1..6:  Y_s = psi + h sum_{q<s} a_sq K_q        (producer warps, FP32)
-//                  K_s = M Y_s                              (tcgen05, BF16x6 -> FP32)
-//   control:       error norm, accept/reject, outputs from the continuous
-//                  extension, crossing root find, jump, refill   (one warp per column)
+//   for s = 1..7:  wt_s = 2^-e M wt_{s-1}, wt_0 = psi       (tcgen05, BF16x6 -> FP32;
+//                                                            producers only split wt_{s-1})
+//   control:       ynew = psi + sum_k beta_k H^k wt_k, the error estimate
+//                  sum_k gamma_k H^k wt_k (H = h 2^e), accept/reject, outputs from
+//                  the continuous extension, crossing root find, jump, refill
+//                  (one warp per column)
+//
+// wt_1 is formed by a product every attempt (seven products, the stage form's six
+// plus one): carried over from the last step by a combination instead, as the
+// double-float SIMT kernel does, its FP32 rounding would drift from step to step
+// (measured: median jump-time error 2.9e-5 against the oracle instead of < 1e-5).
 //
 // The product is D[col][i] = sum_k Y[col][k] Mr[i][k] with the real form
 // Mr = [[Re M, -Im M], [Im M, Re M]] (2N x 2N) and Y = (Re y, Im y): M = 128 columns,
@@ -21,13 +31,13 @@
 // Y1M1, Y0M2) are accumulated in FP32: the dropped terms are of relative size
 // 2^-24, so the product is as accurate as an FP32 one.  (Two terms and three
 // products leave 2^-16, far above the 1e-8 tolerances, and the step-size control
-// then shrinks the steps to chase the product's noise.)  Each k-block of Y is
-// formed in registers from psi and the earlier K_q (read once from device
-// memory), split, and written straight into the 128-byte-swizzled K-major layout
-// the tensor core reads; the operator's splits stream in by TMA, one 256-row
+// then shrinks the steps to chase the product's noise.)  Each k-block of the
+// input wt_s is read once from device memory, split, and written straight into
+// the 128-byte-swizzled K-major layout the tensor core reads (the operator's
+// splits are scaled by 2^-e on the host, exactly); the operator's splits stream in by TMA, one 256-row
 // chunk of one split per ring entry (three-deep ring, L2-resident).  The FP32
 // accumulators (128 lanes x 2N columns) sit in tensor memory until the epilogue
-// warps move them to K_s in device memory.
+// warps move them to wt_{s+1} in device memory.
 //
 // Warp roles (320 threads): warp 0 TMA, warp 1 tensor-memory owner and MMA
 // issuer, warps 2..9 producers, epilogue and per-column control.  Every mbarrier
@@ -48,7 +58,7 @@ constexpr int kThreadsTc = 320;
 constexpr int kProducers = 256;
 constexpr int kKB = 64;               // k-block: 64 bf16 = one 128-byte row
 constexpr int kYTile = 128 * 128;     // bytes of one bf16 Y tile (128 rows x 128 B)
-constexpr int kCoefFloats = 49 + 7 + 35;
+constexpr int kCoefFloats = 50;  // KCoefs<ArF32>: beta[7], Q[5][8], gamma[3]
 constexpr int kStatusTimeout = 8;  // QTM_ERR_TIMEOUT
 constexpr int kSplits = 3;         // bf16 terms per operand
 constexpr int kOpRing = 3;         // operator ring entries
@@ -74,9 +84,13 @@ struct TcShape {
     static_assert(HALF % 16 == 0, "epilogue loads 16 columns at a time");
 };
 
-// Coefficient table layout (FP32): a[s][q] at 7 s + q, e[q] at 49 + q, W[j][m-1] at 56 + 5 j + m - 1.
-__device__ __forceinline__ float cE(const float *cf, int q) { return cf[49 + q]; }
-__device__ __forceinline__ const float *cW(const float *cf) { return cf + 56; }
+// The coefficient table is the Krylov form's KCoefs<ArF32> (beta, Q, gamma).
+__device__ __forceinline__ const KCoefs<ArF32> &kcoefs(const float *cf)
+{
+    return *reinterpret_cast<const KCoefs<ArF32> *>(cf);
+}
+// State-vector index of wt_k (k = 1..7): the seven slots after the two psi buffers
+__device__ __forceinline__ int wvec(int k) { return kVK0 + k - 1; }
 
 struct Ctl {
     const DenseArgs *a;
@@ -196,11 +210,10 @@ __device__ void role_mma(const DenseArgs &a, Pipe &p)
     tc::mma_commit(p.acc_full);
 }
 
-// The eight rows of one k-block a producer thread forms for stage SS (0: the
-// rhs-mode input): Y_s = psi + h sum_{q<s} a_sq K_q from device memory (the
-// coefficients are compile-time constants, so only the K_q with a_sq != 0 are
-// read, all loads issued before the combination), split into three bf16 terms
-// and stored into the swizzled tiles.
+// The eight rows of one k-block a producer thread forms for product SS (0: the
+// rhs-mode input): the input wt_{SS-1} of the column (wt_0 = psi) read from device
+// memory, split into three bf16 terms and stored into the swizzled tiles (idle
+// columns: zero).
 template <int NP, int SS>
 __device__ __forceinline__ void produce_rows(const DenseArgs &a, long long tile_base, int pw, int lane, int kg,
                                              const float *s_hf, const int *s_sel, unsigned char *ytile)
@@ -216,26 +229,9 @@ __device__ __forceinline__ void produce_rows(const DenseArgs &a, long long tile_
             const long long g = tile_base + row;
             if (g < a.rhs_n) y = ld4(a.rhs_in + g * KD + kg);
         } else {
-            const float hf = s_hf[row];
-            if (hf != 0.f) {
-                const int sel = s_sel[row];
-                float *base = a.state + (size_t)(tile_base + row) * KD + kg;
-                y = ld4(base + (sel & 1) * vs);
-                float4 kv[SS];
-                kv[0] = ld4(base + (kVK0 + ((sel & 2) ? 6 : 0)) * vs);
-#pragma unroll
-                for (int q = 1; q < SS; ++q)
-                    if (DP5::a(SS, q) != 0.0) kv[q] = ld4(base + (kVK0 + q) * vs);
-#pragma unroll
-                for (int q = 0; q < SS; ++q)
-                    if (DP5::a(SS, q) != 0.0) {
-                        const float w = hf * (float)DP5::a(SS, q);
-                        y.x = fmaf(w, kv[q].x, y.x);
-                        y.y = fmaf(w, kv[q].y, y.y);
-                        y.z = fmaf(w, kv[q].z, y.z);
-                        y.w = fmaf(w, kv[q].w, y.w);
-                    }
-                if constexpr (SS == 6) st4(base + (1 - (sel & 1)) * vs, y);  // the candidate ynew
+            if (s_hf[row] != 0.f) {
+                const int v = SS == 1 ? (s_sel[row] & 1) : kVK0 + SS - 2;  // psi, or wt_{SS-1}
+                y = ld4(a.state + (size_t)(tile_base + row) * KD + kg + v * vs);
             }
         }
         uint2 t[kSplits];
@@ -269,7 +265,8 @@ __device__ void role_producer(const DenseArgs &a, Pipe &p, int s, long long tile
         case 3: produce_rows<NP, 3>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
         case 4: produce_rows<NP, 4>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
         case 5: produce_rows<NP, 5>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
-        default: produce_rows<NP, 6>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
+        case 6: produce_rows<NP, 6>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
+        default: produce_rows<NP, 7>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
         }
         tc::fence_proxy_async_smem();
         tc::mbar_arrive(&p.y_full[ys]);
@@ -293,9 +290,7 @@ __device__ void role_producer(const DenseArgs &a, Pipe &p, int s, long long tile
         if (g < a.rhs_n) dst = a.rhs_out + g * S::KD;
     } else {
         const Ctl c{&a, (int)(tile_base + row), NP, S::KD};
-        const int sel = s_sel[row];
-        const int slot = s == 6 ? ((sel & 2) ? 0 : 6) : s;
-        dst = c.vec(kVK0 + slot);
+        dst = c.vec(wvec(s));  // wt_s
     }
     const uint32_t tbase = p.tmem + ((uint32_t)(32 * quarter) << 16);
     // 64 columns per round: four loads in flight, one wait
@@ -360,6 +355,15 @@ struct ColCtl {
     __device__ float re(int v, int m) const { return c.vec(v)[m]; }
     __device__ float im(int v, int m) const { return c.vec(v)[NP + m]; }
     __device__ CsrView<Arc> op(int i) const { return csr_view<Arc>(k.op[i], k.ints, (const float *)k.vals); }
+    // 2^-e as a float and H^q = (h 2^e)^q, q = 0..7, for the Krylov coefficients
+    __device__ float down() const { return __int_as_float((127 - k.krylov_shift) << 23); }
+    __device__ void powers(double h, float (&hp)[8]) const
+    {
+        const float H = (float)(h * ldexp(1.0, k.krylov_shift));
+        hp[0] = 1.f;
+#pragma unroll
+        for (int q = 1; q < 8; ++q) hp[q] = hp[q - 1] * H;
+    }
 
     // v[r] = (A_i x)[lane + 32 r] for x = scr, every row of the lane at once.
     // Dense operators: column-major FP32 copy, a column's 32 consecutive rows per
@@ -453,27 +457,34 @@ struct ColCtl {
         }
     }
 
-    // scr <- psi + h sum_j w_j(theta) K_j (the continuous extension) for rows < n
+    // scr <- psi + sum_k rho_k(theta) H^k wt_k (the continuous extension) for rows < n
     __device__ __forceinline__ void dense_to_scr(const DenseCol &d, double th) const
     {
-        float w[7];
-        Arc::weights(th, cW(cf), w);
-        const float hf = (float)d.h;
-        const int pv = d.sel & 1, k0 = (d.sel & 2) ? 6 : 0;
+        const KCoefs<ArF32> &KC = kcoefs(cf);
+        float hp[8];
+        powers(d.h, hp);
+        const float tf = (float)th;
+        float dk[8];
+#pragma unroll
+        for (int q = 1; q < 8; ++q) {
+            float p = KC.Q[4][q];
+#pragma unroll
+            for (int m = 3; m >= 0; --m) p = fmaf(p, tf, KC.Q[m][q]);
+            dk[q] = p * tf * hp[q];
+        }
+        const int pv = d.sel & 1;
 #pragma unroll 4
         for (int r = 0; r < R; ++r) {
             const int m = lane + 32 * r;
             if (m >= k.n) continue;
-            float ar = 0.f, ai = 0.f;
+            float ar = re(pv, m), ai = im(pv, m);
 #pragma unroll
-            for (int j = 0; j < 7; ++j) {
-                if (j == 1) continue;
-                const int v = kVK0 + (j == 0 ? k0 : j == 6 ? 6 - k0 : j);
-                ar = fmaf(w[j], re(v, m), ar);
-                ai = fmaf(w[j], im(v, m), ai);
+            for (int q = 1; q < 8; ++q) {
+                ar = fmaf(dk[q], re(wvec(q), m), ar);
+                ai = fmaf(dk[q], im(wvec(q), m), ai);
             }
-            scr[2 * m] = fmaf(hf, ar, re(pv, m));
-            scr[2 * m + 1] = fmaf(hf, ai, im(pv, m));
+            scr[2 * m] = ar;
+            scr[2 * m + 1] = ai;
         }
         __syncwarp();
     }
@@ -519,8 +530,8 @@ struct ColCtl {
         __syncwarp();
     }
 
-    // K-slot vector v <- M scr (rows < n; padded rows stay zero)
-    __device__ __noinline__ void rhs_to(int v) const
+    // state vector v <- scale M scr (rows < n; padded rows stay zero)
+    __device__ __noinline__ void rhs_to(int v, float scale) const
     {
         cf32 y[R];
         opmv(0, y);
@@ -529,8 +540,8 @@ struct ColCtl {
         for (int r = 0; r < R; ++r) {
             const int m = lane + 32 * r;
             if (m < k.n) {
-                dst[m] = y[r].re;
-                dst[NP + m] = y[r].im;
+                dst[m] = scale * y[r].re;
+                dst[NP + m] = scale * y[r].im;
             }
         }
     }
@@ -542,36 +553,32 @@ struct ColCtl {
         double gram[21];
 #pragma unroll
         for (int q = 0; q < 21; ++q) gram[q] = 0.0;
-        const float hf = (float)d.h;
-        const int pv = d.sel & 1, k0 = (d.sel & 2) ? 6 : 0;
-        const float *W = cW(cf);
+        const KCoefs<ArF32> &KC = kcoefs(cf);
+        float hp[8];
+        powers(d.h, hp);
+        const int pv = d.sel & 1;
         for (int r = 0; r < R; ++r) {
             const int m = lane + 32 * r;
             if (m >= k.n) continue;
             float ur[6], ui[6];
             ur[0] = re(pv, m);
             ui[0] = im(pv, m);
-            float kr[7], ki[7];
+            float kr[8], ki[8];
 #pragma unroll
-            for (int j = 0; j < 7; ++j) {
-                if (j == 1) {
-                    kr[j] = ki[j] = 0.f;
-                    continue;
-                }
-                const int v = kVK0 + (j == 0 ? k0 : j == 6 ? 6 - k0 : j);
-                kr[j] = re(v, m);
-                ki[j] = im(v, m);
+            for (int q = 1; q < 8; ++q) {
+                kr[q] = hp[q] * re(wvec(q), m);
+                ki[q] = hp[q] * im(wvec(q), m);
             }
 #pragma unroll
             for (int mm = 1; mm <= 5; ++mm) {
                 float sr = 0.f, si = 0.f;
 #pragma unroll
-                for (int j = 0; j < 7; ++j) {
-                    sr = fmaf(W[5 * j + mm - 1], kr[j], sr);
-                    si = fmaf(W[5 * j + mm - 1], ki[j], si);
+                for (int q = 1; q < 8; ++q) {
+                    sr = fmaf(KC.Q[mm - 1][q], kr[q], sr);
+                    si = fmaf(KC.Q[mm - 1][q], ki[q], si);
                 }
-                ur[mm] = hf * sr;
-                ui[mm] = hf * si;
+                ur[mm] = sr;
+                ui[mm] = si;
             }
             int q = 0;
 #pragma unroll
@@ -779,7 +786,7 @@ struct ColCtl {
             __syncwarp();
             output(d, 0);
             d.j = 1;
-            rhs_to(kVK0);
+            rhs_to(wvec(1), 1.f);  // K_0 = M psi0 for the starting step (wt_1 is formed by the products)
             ++d.n_rhs;
             // starting step (Hairer, Norsett & Wanner, Sec. II.4)
             const double span = t_end - d.t;
@@ -827,74 +834,64 @@ struct ColCtl {
         }
     }
 
-    // After the six products of an attempt.
-    // Tail mode: the six stage products of one attempt on this warp alone, with
-    // the control's own operator copy (FP32 products), leaving K_1..K_6 and ynew
-    // where the tensor-core stages put them.
+    // Tail mode: the seven products of one attempt on this warp alone, with the
+    // control's own operator copy (FP32 products): wt_s = 2^-e M wt_{s-1}, wt_0 = psi,
+    // where the tensor-core products put them.
     __device__ __noinline__ void simt_products(const DenseCol &d) const
     {
-        const float hf = (float)d.h;
-        const int pv = d.sel & 1, k0 = (d.sel & 2) ? 6 : 0;
-        float *yn = c.vec(1 - pv);
-        for (int s = 1; s <= 6; ++s) {
-            for (int r = 0; r < R; ++r) {
-                const int m = lane + 32 * r;
-                if (m >= k.n) continue;
-                float yr = re(pv, m), yi = im(pv, m);
-                for (int q = 0; q < s; ++q) {
-                    const float w = hf * cf[7 * s + q];
-                    if (w == 0.f) continue;
-                    const int v = kVK0 + (q == 0 ? k0 : q);
-                    yr = fmaf(w, re(v, m), yr);
-                    yi = fmaf(w, im(v, m), yi);
-                }
-                scr[2 * m] = yr;
-                scr[2 * m + 1] = yi;
-                if (s == 6) {
-                    yn[m] = yr;
-                    yn[NP + m] = yi;
-                }
-            }
-            __syncwarp();
+        const float dn = down();
+        for (int s = 1; s <= 7; ++s) {
+            vec_to_scr(s == 1 ? (d.sel & 1) : wvec(s - 1));
             cf32 v[R];
             opmv(0, v);
-            float *dst = c.vec(kVK0 + (s == 6 ? 6 - k0 : s));
+            float *dst = c.vec(wvec(s));
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int m = lane + 32 * r;
                 if (m < k.n) {
-                    dst[m] = v[r].re;
-                    dst[NP + m] = v[r].im;
+                    dst[m] = dn * v[r].re;
+                    dst[NP + m] = dn * v[r].im;
                 }
             }
             __syncwarp();
         }
     }
 
+    // After the six products of an attempt.
     __device__ void step(DenseCol &d) const
     {
         const double t_end = k.t[k.n_t - 1];
-        const float hf = (float)d.h;
-        const int pv = d.sel & 1, k0 = (d.sel & 2) ? 6 : 0;
-        d.n_rhs += 6;
+        const KCoefs<ArF32> &KC = kcoefs(cf);
+        float hp[8];
+        powers(d.h, hp);
+        float cb[7];
+#pragma unroll
+        for (int q = 1; q < 7; ++q) cb[q] = KC.beta[q] * hp[q];
+        const float g5 = KC.gam[0] * hp[5], g6 = KC.gam[1] * hp[6], g7 = KC.gam[2] * hp[7];
+        const int pv = d.sel & 1;
+        float *yn = c.vec(1 - pv);
+        d.n_rhs += 7;
         ++d.attempts;
-        // error estimate h sum_q e_q K_q, scaled RMS; squared norm of ynew
+        // the 5th-order solution psi + sum_k beta_k H^k wt_k, its squared norm, and
+        // the error estimate sum_k gamma_k H^k wt_k (no cancellation), scaled RMS
         float esum = 0.f;
         Arc::red nr = Arc::rzero();
 #pragma unroll 4
         for (int r = 0; r < R; ++r) {
             const int m = lane + 32 * r;
             if (m >= k.n) continue;
-            float er = 0.f, ei = 0.f;
+            const cf32 y0{re(pv, m), im(pv, m)};
+            float yr = y0.re, yi = y0.im;
 #pragma unroll
-            for (int q = 0; q < 7; ++q) {
-                if (q == 1) continue;
-                const int v = kVK0 + (q == 0 ? k0 : q == 6 ? 6 - k0 : q);
-                er = fmaf(cE(cf, q), re(v, m), er);
-                ei = fmaf(cE(cf, q), im(v, m), ei);
+            for (int q = 1; q < 7; ++q) {
+                yr = fmaf(cb[q], re(wvec(q), m), yr);
+                yi = fmaf(cb[q], im(wvec(q), m), yi);
             }
-            const cf32 y0{re(pv, m), im(pv, m)}, y1{re(1 - pv, m), im(1 - pv, m)};
-            const float ere = hf * er, eim = hf * ei;
+            yn[m] = yr;
+            yn[NP + m] = yi;
+            const float ere = fmaf(g5, re(wvec(5), m), fmaf(g6, re(wvec(6), m), g7 * re(wvec(7), m)));
+            const float eim = fmaf(g5, im(wvec(5), m), fmaf(g6, im(wvec(6), m), g7 * im(wvec(7), m)));
+            const cf32 y1{yr, yi};
             const float ay2 = y0.re * y0.re + y0.im * y0.im, an2 = y1.re * y1.re + y1.im * y1.im;
             const float sc = (float)k.atol + (float)k.rtol * sqrtf(ay2 > an2 ? ay2 : an2);
             esum += (ere * ere + eim * eim) / (sc * sc);
@@ -945,9 +942,7 @@ struct ColCtl {
             // (D)
             ++d.k;
             jump_draws(k.seed, k.traj0 + d.il, d.k, d.r, d.c);
-            d.t = tau;
-            rhs_to(kVK0 + k0);  // K_0 = M psi after the jump
-            ++d.n_rhs;
+            d.t = tau;  // the next attempt's products start from the new psi
             d.flags &= ~1;
             if (!prepare(d)) refill(d);
             return;
@@ -964,7 +959,7 @@ struct ColCtl {
         if ((d.flags & 1) && fac > 1.0) fac = 1.0;
         d.flags &= ~1;
         d.t = t_new;
-        d.sel ^= 3;  // ynew becomes psi, K_6 becomes K_0
+        d.sel ^= 1;  // ynew becomes psi
         d.h *= fac;
         if (!prepare(d)) refill(d);
     }
@@ -989,17 +984,9 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     int *s_mode = reinterpret_cast<int *>(sm + S::OFF_MISC + 40);  // next attempt: 0 products, 1 tail, 2 done
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    for (int i = threadIdx.x; i < kCoefFloats; i += kThreadsTc) {
-        float v;
-        if (i < 49)
-            v = (i % 7) < 6 ? (float)DP5::a(i / 7, i % 7) : 0.f;
-        else if (i < 56)
-            v = (float)DP5::e(i - 49);
-        else
-            v = (float)DP5::W((i - 56) / 5, (i - 56) % 5 + 1);
-        cf[i] = v;
-    }
+    static_assert(sizeof(KCoefs<ArF32>) == kCoefFloats * sizeof(float), "coefficient table size");
     if (threadIdx.x == 0) {
+        krylov_coefs<ArF32>(reinterpret_cast<KCoefs<ArF32> *>(cf));
         for (int i = 0; i < 2 * kOpRing; ++i) tc::mbar_init(&bars[i], 1);  // op full / empty
         for (int i = 0; i < 2; ++i) tc::mbar_init(&bars[2 * kOpRing + i], kProducers);  // y_full
         for (int i = 2; i < 5; ++i) tc::mbar_init(&bars[2 * kOpRing + i], 1);  // y_empty, acc_full
@@ -1087,7 +1074,7 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
                 __syncthreads();
                 continue;
             }
-            for (int s = 1; s <= 6; ++s) stage_product<NP>(a, p, &opmap, s, tile_base, s_hf, s_sel, cf);
+            for (int s = 1; s <= 7; ++s) stage_product<NP>(a, p, &opmap, s, tile_base, s_hf, s_sel, cf);
             if (warp >= 2 && !*s_abort) {
                 const int pw = warp - 2;
                 ColCtl<NP> cc{a, a.k, Group<32>(threadIdx.x, nullptr), lane, Ctl{&a, 0, NP, S::KD},

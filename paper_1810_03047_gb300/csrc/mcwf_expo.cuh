@@ -209,6 +209,54 @@ struct Expo {
         return const_cast<cplx *>(cur);
     }
 
+    // The bracket [m delta, (m + 1) delta) holding the predicted crossing time
+    // s_hat, formed from the binary digits of m (the levels the descent would keep,
+    // in its order) and checked with one more product.  True on a hit (base, cur,
+    // nb describe the bracket's start); otherwise base, cur, nb are where the
+    // descent has to continue from (psi and 0 when the crossing lies earlier).
+    // Out of line: the crossing search is rare and its registers stay out of the
+    // propagation loop.
+    __device__ __noinline__ bool predicted_bracket(double d, const cplx *psi, double r, double s_hat, const cplx *&base,
+                                                   double &cur, double &nb)
+    {
+        const int L = a.expo_levels - 1;
+        const double delta = a.expo_delta;
+        const double mmax = ceil(d / delta) - 1.0;
+        double md = floor(s_hat / delta);
+        if (md > mmax) md = mmax;
+        if (md < 0.0) md = 0.0;
+        const unsigned long long m = (unsigned long long)md;
+        double nm = nb;
+        base = psi;
+#pragma unroll 1
+        for (int l = L; l >= 0; --l)
+            if ((m >> l) & 1ULL) {
+                cplx *o = (base == A) ? B : A;
+                nm = apply_level(l, base, o);
+                base = o;
+            }
+        if (!(nm >= r)) {  // the crossing lies earlier: descend from psi
+            base = psi;
+            cur = 0.0;
+            ++n_miss;
+            return false;
+        }
+        cur = md * delta;
+        nb = nm;
+        if (cur + delta >= d) return true;  // the interval ends inside the last delta
+        cplx *o = (base == A) ? B : A;
+        const double n1 = apply_level(0, base, o);
+        if (n1 < r) {
+            ++n_rej;
+            return true;
+        }
+        base = o;  // the crossing lies later: descend from the end of this delta
+        cur += delta;
+        nb = n1;
+        ++n_miss;
+        return false;
+    }
+
     // (B) with ||psi||^2 = nb >= r now and ||exp(d M) psi||^2 < r: the time s in
     // (0, d] of the crossing; psi(s) is left in *out (A or B, synchronised).
     // s_hat >= 0 is a predicted crossing time (the learned proposal): the bracket
@@ -223,44 +271,7 @@ struct Expo {
         const double delta = a.expo_delta;
         const cplx *base = psi;
         double cur = 0.0;
-        bool bracketed = false;
-        if (s_hat >= 0.0) {
-            const double mmax = ceil(d / delta) - 1.0;
-            double md = floor(s_hat / delta);
-            if (md > mmax) md = mmax;
-            if (md < 0.0) md = 0.0;
-            const unsigned long long m = (unsigned long long)md;
-            double nm = nb;
-#pragma unroll 1
-            for (int l = L; l >= 0; --l)
-                if ((m >> l) & 1ULL) {
-                    cplx *o = (base == A) ? B : A;
-                    nm = apply_level(l, base, o);
-                    base = o;
-                }
-            if (nm >= r) {
-                cur = md * delta;
-                nb = nm;
-                if (cur + delta >= d) {
-                    bracketed = true;  // the interval ends inside the last delta
-                } else {
-                    cplx *o = (base == A) ? B : A;
-                    const double n1 = apply_level(0, base, o);
-                    if (n1 < r) {
-                        bracketed = true;
-                        ++n_rej;
-                    } else {  // the crossing lies later: descend from the end of this delta
-                        base = o;
-                        cur += delta;
-                        nb = n1;
-                        ++n_miss;
-                    }
-                }
-            } else {  // the crossing lies earlier: descend from psi
-                base = psi;
-                ++n_miss;
-            }
-        }
+        const bool bracketed = s_hat >= 0.0 && predicted_bracket(d, psi, r, s_hat, base, cur, nb);
         // binary descent: keep level l when the norm after it is still >= r (a
         // level ending at d would not be kept: the norm there is below r)
         if (!bracketed) {
@@ -406,6 +417,40 @@ struct ExpoProp {
 };
 constexpr int kExpoPropStride = (int)((sizeof(ExpoProp) + 15) & ~size_t(15));
 
+// The proposal's work at a crossing, out of line so that it adds no register
+// pressure to the propagation loop: the features of the interval (x.t, x.t + d]
+// with norms nb and nn at its ends, a training record (collection mode; *rec is
+// left pointing at it so that the caller can store the crossing's time), and the
+// predicted time of the crossing from x.t (-1 without a network).
+template <int G>
+__device__ __noinline__ double expo_predict(const KernelArgs &a, const Group<G> &g, ExpoProp *PS, double nb,
+                                            double nn, double d, double r, unsigned long long n_jump, long long il,
+                                            float **rec)
+{
+    // FP32 features (like the network), so the narrow FP64 pipe is not used for them
+    const float gam = __logf((float)nb / (float)nn) / (float)d;
+    *rec = nullptr;
+    if (g.gl == 0) {
+        PS->f[0] = gam;
+        PS->f[1] = PS->gam_prev > 0.f ? (gam - PS->gam_prev) / (float)d : 0.f;
+        PS->f[2] = (float)nb;
+        PS->f[3] = __logf((float)r);
+        if (a.rec_stride > 0 && (long long)(n_jump % a.rec_stride) == 0 && PS->rec_n < a.rec_max) {
+            float *q = a.rec + ((size_t)il * a.rec_max + PS->rec_n++) * kRecFloats;
+            for (int i = 0; i < kMlpIn; ++i) q[i] = PS->f[i];
+            q[6] = 0.f;
+            *rec = q;
+        }
+    }
+    if (!a.mlp) return -1.0;
+    const float y = mlp_eval<G>(g, a.mlp, PS->f, PS->h);  // synchronises before reading f
+    const float est = (__logf((float)nb) - __logf((float)r)) / gam;
+    double s_hat = (double)(est * __expf(y));
+    if (!(s_hat >= 0.0)) s_hat = 0.0;
+    if (s_hat > d) s_hat = d;
+    return s_hat;
+}
+
 // Per-trajectory scalars of a group (indexed at run time; they live in local memory).
 struct ExpoTraj {
     double t, r, c, nb;
@@ -507,28 +552,7 @@ __device__ void run_group_expo(const KernelArgs &a, const Group<G> &g, const int
                 const double d = a.t[j] - x.t;
                 double s_hat = -1.0;
                 float *rec = nullptr;
-                if constexpr (PROP) {
-                    // features (lane 0 writes them; mlp_eval synchronises before reading)
-                    const float gam = (float)(log(x.nb / nn) / d);
-                    if (gl == 0) {
-                        PS->f[0] = gam;
-                        PS->f[1] = PS->gam_prev > 0.f ? (gam - PS->gam_prev) / (float)d : 0.f;
-                        PS->f[2] = (float)x.nb;
-                        PS->f[3] = __logf((float)x.r);
-                        if (a.rec_stride > 0 && (long long)(x.n_jump % a.rec_stride) == 0 && PS->rec_n < a.rec_max) {
-                            rec = a.rec + ((size_t)(il0 + t) * a.rec_max + PS->rec_n++) * kRecFloats;
-                            for (int q = 0; q < kMlpIn; ++q) rec[q] = PS->f[q];
-                            rec[6] = 0.f;
-                        }
-                    }
-                    if (a.mlp) {
-                        const float y = mlp_eval<G>(g, a.mlp, PS->f, PS->h);
-                        const double est = (log(x.nb) - log(x.r)) / (double)gam;
-                        s_hat = est * (double)__expf(y);
-                        if (!(s_hat >= 0.0)) s_hat = 0.0;
-                        if (s_hat > d) s_hat = d;
-                    }
-                }
+                if constexpr (PROP) s_hat = expo_predict<G>(a, g, PS, x.nb, nn, d, x.r, x.n_jump, il0 + t, &rec);
                 const double s = E.crossing(d, psi, x.nb, x.r, x.t, &ytau, s_hat);
                 if constexpr (PROP)
                     if (rec) rec[7] = (float)s;
@@ -562,7 +586,7 @@ __device__ void run_group_expo(const KernelArgs &a, const Group<G> &g, const int
                 continue;
             }
             if constexpr (PROP)  // the decay rate over this (jump-free) stretch, for the next crossing's features
-                if (gl == 0) PS->gam_prev = (float)(log(x.nb / nn) / (a.t[j] - x.t));
+                if (gl == 0) PS->gam_prev = __logf((float)x.nb / (float)nn) / (float)(a.t[j] - x.t);
             record_outputs<Ar, G, R>(a, g, si, sv, y, j, a.out + (size_t)(il0 + t) * a.n_t * a.n_obs,
                                      PROP ? PS->f + 4 : nullptr);
 #pragma unroll

@@ -533,14 +533,17 @@ float bf16_value(uint16_t b)
 // of M (2 np x 2 np, zero-padded), row i = output, column k = input, split into
 // three bf16 terms x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1):
 // out = [x0 rows][x1 rows][x2 rows].
-std::vector<uint16_t> tc_operator(const Csr &M, int np)
+// The engine's operator: the real form of 2^-shift M (the Krylov form's scaled
+// operator; scaling by a power of two is exact), split into three bf16 terms.
+std::vector<uint16_t> tc_operator(const Csr &M, int np, int shift)
 {
     const int kd = 2 * np;
+    const double sc = std::ldexp(1.0, -shift);
     std::vector<double> mr((size_t)kd * kd, 0.0);
     for (int i = 0; i < M.n; ++i)
         for (int e = M.rp[i]; e < M.rp[i + 1]; ++e) {
             const int k = M.ci[e];
-            const double re = M.val[e].real(), im = M.val[e].imag();
+            const double re = sc * M.val[e].real(), im = sc * M.val[e].imag();
             mr[(size_t)i * kd + k] = re;
             mr[(size_t)i * kd + np + k] = -im;
             mr[(size_t)(np + i) * kd + k] = im;
@@ -593,7 +596,7 @@ qtm_status tc_make_map(qtm_ctx *ctx)
 qtm_status tc_setup(qtm_ctx *ctx)
 {
     ctx->np = qtm::tc_padded_dim(ctx->n);
-    std::vector<uint16_t> op = tc_operator(ctx->M, ctx->np);
+    std::vector<uint16_t> op = tc_operator(ctx->M, ctx->np, ctx->krylov_shift);
     std::vector<const Csr *> all{&ctx->M};
     for (const Csr &c : ctx->Cops) all.push_back(&c);
     for (const Csr &a : ctx->Aops) all.push_back(&a);
@@ -1706,10 +1709,12 @@ qtm_status qtm_rhs_batch(qtm_ctx *ctx, int64_t n_vec, const double *y, double *m
     if ((e = cudaMemcpy(&first, d_status, sizeof(int), cudaMemcpyDeviceToHost)))
         return cuda_fail(ctx, e, "qtm_rhs_batch: status");
     if (first) return fail(ctx, (qtm_status)first, "qtm_rhs_batch: a device wait gave up");
+    // the engine's operator is 2^-shift M: scale back (exact)
+    const double up = std::ldexp(1.0, ctx->krylov_shift);
     for (int64_t v = 0; v < n_vec; ++v)
         for (int i = 0; i < n; ++i) {
-            my[2 * ((size_t)v * n + i)] = res[(size_t)v * kd + i];
-            my[2 * ((size_t)v * n + i) + 1] = res[(size_t)v * kd + np + i];
+            my[2 * ((size_t)v * n + i)] = up * res[(size_t)v * kd + i];
+            my[2 * ((size_t)v * n + i) + 1] = up * res[(size_t)v * kd + np + i];
         }
     return QTM_OK;
 }

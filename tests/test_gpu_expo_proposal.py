@@ -98,7 +98,7 @@ def test_expo_proposal_same_jumps_fewer_products(trained_expo, prec, capsys):
               f"trajectory {p_off:.1f} -> {p_on:.1f} ({100 * (p_off - p_on) / p_off:+.2f} %), bracket hits "
               f"{100 * (1 - misses / max(jumps, 1)):.1f} %, jump times bitwise equal "
               f"{100 * same / max(total, 1):.1f} %, largest relative difference {worst:.2e}, loss "
-              f"{trained_expo['loss']:.4f} vs constant-rate {trained_expo['base']:.4f}")
+              f"{trained_expo['loss']:.3e} vs constant-rate {trained_expo['base']:.3e}")
     np.testing.assert_array_equal(on["n_jumps"], off["n_jumps"])
     for i in range(n):
         k = min(int(off["n_jumps"][i]), MAXJ)
