@@ -55,9 +55,10 @@ RUN_LAUNCHES = 3
 # `python bench.py --only df64 --steps 1 --warmup 1` (-k regex:mcwf_kernel) and
 # `python bench.py --only dense --steps 1 --warmup 1` (-k regex:dense_tc_kernel).
 # Valid for the kernels as captured; a change to a kernel voids its entry.
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch at the bench's size
+# (one ncu pass, profiles/); an entry is removed when its kernel changes
 TRAFFIC_PER_LAUNCH = {
-    "qtm::mcwf_kernel<df64,32,2>": 4.82e6 + 101.55e6,    # 20,000 JC trajectories: the outputs
-    "qtm::dense_tc_kernel<256>": 184.81e9 + 51.10e9,     # 20,000 dense trajectories: the state block
+    "qtm::dense_tc_kernel<256>": 54.81e9 + 55.78e9,      # 20,000 dense trajectories, seven products per attempt
 }
 
 
@@ -319,6 +320,25 @@ def measured_arith_peaks(Q, torch, stream, seconds=1.0):
                 iters = max(1000, int(iters * seconds / max(sec, 1e-6)))
         out[name] = best
     return out
+
+
+def _bf16x6_peak(sustained=True):
+    """Peak of the tensor-core engines' FP32-accurate products: the measured bf16
+    dense peak (sustained for kernels inside a long run) over the six bf16
+    products each BF16x6 product issues."""
+    mp = measured_peaks()
+    key = "bf16_tflops_sustained" if sustained else "bf16_tflops"
+    if key in mp:
+        return float(mp[key]) / 6.0, f"measured cuBLAS bf16 peak (MEASURED_PEAKS.json {key}) / 6, of measured"
+    return (1700.0 if sustained else 1900.0) / 6.0, "fallback bf16 peak / 6, of fallback"
+
+
+def lockstep_launches(n_t, every=8):
+    """Kernels of one lock-step exponential run on the tensor cores: a tensor-core
+    product per output interval, the per-interval kernel per output, a catch-up
+    every `every` intervals and after the last, the finish, and the reduction."""
+    catch = sum(1 for j in range(1, n_t) if j % every == 0 or j == n_t - 1)
+    return (n_t - 1) + n_t + catch + 1 + (RUN_LAUNCHES - 1)
 
 
 def _hbm_peak():
@@ -715,10 +735,13 @@ def dense_tensor_core(Q, torch, stream, world, rank, dist, pk, ntraj=20000, samp
     products on tcgen05, FP32 state), 20,000 trajectories per GPU: one warm-up
     pass, two timed.  The plain FP64 GPU path (complex128) runs the first 2,000
     trajectory ids for its throughput and for the observable error on the same
-    trajectories.  Roofline: the engine is bound by device memory -- per attempted
-    step and trajectory it reads psi and the stage vectors 26 times while forming
-    the six stage inputs, writes six stage vectors and ynew, and reads eight vectors
-    for the error estimate: 41 passes over 2N FP32 values."""
+    trajectories.  Roofline: the products are the engine's work -- per attempted
+    step and trajectory seven FP32-accurate products of the scaled operator (8 N^2
+    flops each, the Krylov form's wt_1 .. wt_7), issued as six bf16 tensor-core
+    products each -- against the measured bf16 peak over six.  Its state passes
+    (per attempt: seven product inputs, seven outputs, eight vectors read and one
+    written by the control warps, 23 passes over 2N FP32 values) are reported
+    beside it."""
     from paper_1810_03047_gb300 import shards
     from paper_1810_03047_gb300 import systems as S
     prob = S.dense_random(ntraj=ntraj)
@@ -755,10 +778,12 @@ def dense_tensor_core(Q, torch, stream, world, rank, dist, pk, ntraj=20000, samp
     Q.qtm_destroy(ref)
     err = float(np.abs(tc_traj.mean(axis=0) - ref_traj.mean(axis=0)).max())
     n = prob.dim
-    bytes_per_attempt = 41 * 2 * n * 4
+    bytes_per_attempt = 23 * 2 * n * 4
+    flops_per_attempt = 7 * 8.0 * n * n
     kms = sum(kern) / len(kern)
-    achieved = bytes_per_attempt * (attempts / 2) / (kms / 1e3) / 1e9
-    peak, note = pk["hbm"]
+    achieved = flops_per_attempt * (attempts / 2) / (kms / 1e3) / 1e12
+    peak, note = _bf16x6_peak()
+    hbm_peak, _ = pk["hbm"]
     return {"workload": "dense random open system: GUE H (N=256), 4 Ginibre C_n (||C_n||_2=0.3), 101 outputs on "
                         "[0,10], A = diag(0..N-1)/N, operators default_rng(3), seed 1",
             "precision": "tensor-core BF16x6 products, FP32 state, FP64 scalars", "unit": UNIT,
@@ -768,11 +793,14 @@ def dense_tensor_core(Q, torch, stream, world, rank, dist, pk, ntraj=20000, samp
             "observable_error": err,
             "observable_error_note": f"max |mean - complex128 mean| over the first {sample} trajectory ids",
             "steps_per_trajectory": attempts / 2 / count,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak,
-                         "traffic": TRAFFIC_PER_LAUNCH["qtm::dense_tc_kernel<256>"] if count == 20000 else None,
-                         "kernel": "qtm::dense_tc_kernel<256>",
-                         "bytes_per_attempt": bytes_per_attempt, "peak_note": note, "kernel_ms": kms},
+                         "traffic": TRAFFIC_PER_LAUNCH.get("qtm::dense_tc_kernel<256>") if count == 20000 else None,
+                         "kernel": "qtm::dense_tc_kernel<256>", "flops_per_attempt": flops_per_attempt,
+                         "state_bytes_per_attempt": bytes_per_attempt,
+                         "state_gbs": bytes_per_attempt * (attempts / 2) / (kms / 1e3) / 1e9,
+                         "state_frac_of_hbm": bytes_per_attempt * (attempts / 2) / (kms / 1e3) / 1e9 / hbm_peak,
+                         "peak_note": note, "kernel_ms": kms},
             "launches": 4 * RUN_LAUNCHES}
 
 
@@ -801,9 +829,14 @@ def _timed_passes(Q, torch, stream, world, dist, prob, prec, method, first, coun
     st = Q.qtm_stats(ctx)
     mean = Q.qtm_expect(ctx)[0]
     Q.qtm_destroy(ctx)
-    return {"value": world * count / (float(t.item()) / 1e3), "ms_per_step": float(t.item()),
-            "kernel_ms": st["kernel_ms"], "products_per_trajectory": st["rhs_evals"] / count,
-            "jumps_per_trajectory": st["jumps"] / count, "mean": mean, "launches": (1 + passes) * RUN_LAUNCHES}
+    per_run = lockstep_launches(len(prob.t)) if (prec == Q.QTM_PREC_BF16X6 and method == Q.QTM_METHOD_EXPONENTIAL) \
+        else RUN_LAUNCHES
+    out = {"value": world * count / (float(t.item()) / 1e3), "ms_per_step": float(t.item()),
+           "kernel_ms": st["kernel_ms"], "products_per_trajectory": st["rhs_evals"] / count,
+           "jumps_per_trajectory": st["jumps"] / count, "mean": mean, "launches": (1 + passes) * per_run}
+    if st.get("product_ms"):
+        out["product_ms"] = st["product_ms"]
+    return out
 
 
 def exponential_method(Q, torch, stream, world, rank, dist, pk, jc_ref_mean, ntraj=20000):
@@ -877,8 +910,10 @@ def exponential_method(Q, torch, stream, world, rank, dist, pk, jc_ref_mean, ntr
     # 2,000 ids and the tensor-core engine's figure (reported in its own leg)
     dense = S.dense_random(ntraj=ntraj)
     dres = {}
-    for key, prec in (("expo_df64", Q.QTM_PREC_DF64), ("expo_c128", Q.QTM_PREC_C128), ("expo_c64", Q.QTM_PREC_C64)):
-        dres[key] = _timed_passes(Q, torch, stream, world, dist, dense, prec, E, first, count, passes=1)
+    for key, prec in (("expo_df64", Q.QTM_PREC_DF64), ("expo_c128", Q.QTM_PREC_C128), ("expo_c64", Q.QTM_PREC_C64),
+                      ("expo_tc", Q.QTM_PREC_BF16X6)):
+        dres[key] = _timed_passes(Q, torch, stream, world, dist, dense, prec, E, first, count,
+                                  passes=2 if key == "expo_tc" else 1)
         launches += dres[key].pop("launches")
     sample = min(count, 2000)
     ctx = Q.qtm_create(dense, stream=int(stream.cuda_stream), precision=Q.QTM_PREC_C128)
@@ -888,13 +923,13 @@ def exponential_method(Q, torch, stream, world, rank, dist, pk, jc_ref_mean, ntr
     Q.qtm_destroy(ctx)
     launches += RUN_LAUNCHES
     ex_traj = {}
-    for key, prec in (("expo_df64", Q.QTM_PREC_DF64), ("expo_c64", Q.QTM_PREC_C64)):
+    for key, prec in (("expo_df64", Q.QTM_PREC_DF64), ("expo_c64", Q.QTM_PREC_C64), ("expo_tc", Q.QTM_PREC_BF16X6)):
         ctx = Q.qtm_create(dense, stream=int(stream.cuda_stream), precision=prec)
         Q.qtm_set_method(ctx, E)
         Q.qtm_run_range(ctx, first, sample, dense.seed)
         ex_traj[key] = Q.qtm_traj_expect(ctx)
         Q.qtm_destroy(ctx)
-        launches += RUN_LAUNCHES
+        launches += lockstep_launches(len(dense.t)) if key == "expo_tc" else RUN_LAUNCHES
     nd = dense.dim
     dj = {"workload": "dense random open system (GUE H, N=256, 4 Ginibre C_n), 101 outputs on [0, 10], "
                       f"{world * count} trajectories", "unit": UNIT,
@@ -903,6 +938,8 @@ def exponential_method(Q, torch, stream, world, rank, dist, pk, jc_ref_mean, ntr
                                                                     - ref_traj.mean(axis=0)).max()),
           "observable_error_expo_c64_vs_dopri5_c128": float(np.abs(ex_traj["expo_c64"].mean(axis=0)
                                                                    - ref_traj.mean(axis=0)).max()),
+          "observable_error_expo_tc_vs_dopri5_c128": float(np.abs(ex_traj["expo_tc"].mean(axis=0)
+                                                                  - ref_traj.mean(axis=0)).max()),
           "observable_error_note": f"max |mean - complex128 Dormand-Prince mean| over the first {sample} ids"}
     for key, peak_key in (("expo_df64", "df64"), ("expo_c128", "c128"), ("expo_c64", "c64")):
         v = dres[key]
@@ -911,6 +948,21 @@ def exponential_method(Q, torch, stream, world, rank, dist, pk, jc_ref_mean, ntr
         dj[key] = {kk: vv for kk, vv in v.items() if kk != "mean"}
         dj[key]["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                                "frac": achieved / peak, "traffic": None, "peak_note": note}
+    # the lock-step path on the tensor cores: its product launch against the
+    # BF16x6 emulation peak (one (P_L - I) psi of 8 N^2 flops per trajectory)
+    v = dres["expo_tc"]
+    dj["expo_tc"] = {kk: vv for kk, vv in v.items() if kk != "mean"}
+    dj["expo_tc"]["precision"] = ("tensor-core BF16x6 products (P_L - I) psi for all trajectories per output "
+                                  "interval, complex64 crossing search, jumps and outputs")
+    dj["expo_tc"]["speedup_vs_expo_c64"] = v["value"] / dres["expo_c64"]["value"]
+    if v.get("product_ms"):
+        peak, note = _bf16x6_peak()
+        achieved = 8.0 * nd * nd * count / (v["product_ms"] / 1e3) / 1e12
+        dj["expo_tc"]["roofline"] = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                                     "frac": achieved / peak, "traffic": None,
+                                     "kernel": "qtm::dense_tc_kernel<256> (rhs mode, (P_L - I) psi)",
+                                     "flops_per_launch": 8.0 * nd * nd * count, "kernel_ms": v["product_ms"],
+                                     "peak_note": note}
     out["dense_random"] = dj
     out["launches"] = launches
     return out

@@ -163,6 +163,9 @@ typedef struct {
     double reduce_ms;          /* device time of the ensemble reduction */
     int64_t proposal_misses;   /* exponential method with the learned proposal: crossings whose predicted
                                   bracket missed (the search then descended as without a prediction) */
+    double product_ms;         /* exponential method on the tensor cores (QTM_PREC_BF16X6): device time of
+                                  one tensor-core product launch, (P_L - I) applied to every trajectory (the
+                                  first output interval's launch); 0 otherwise */
 } qtm_stats_t;
 
 typedef struct qtm_ctx qtm_ctx;

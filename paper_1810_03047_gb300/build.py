@@ -56,7 +56,14 @@ def _compile(src: str, extra=()) -> str:
     obj = os.path.join(BUILD, os.path.basename(src) + ".o")
     cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *PER_FILE_FLAGS.get(os.path.basename(src), []), *extra, "-c", src,
            "-o", obj]
-    r = subprocess.run(cmd, capture_output=True, text=True)
+    # a compiler process that dies on a signal (seen once: a segmentation fault
+    # of one of the parallel nvcc processes, not reproducible) is run again; a
+    # diagnosed compile error is not
+    for attempt in range(3):
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        crashed = r.returncode < 0 or "Segmentation fault" in r.stderr or "Killed" in r.stderr
+        if r.returncode == 0 or not crashed:
+            break
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {os.path.basename(src)}:\n{r.stdout}\n{r.stderr}")
     return obj

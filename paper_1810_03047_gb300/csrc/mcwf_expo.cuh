@@ -98,7 +98,7 @@ __device__ __forceinline__ void level_apply(const typename Ar::cplx *__restrict_
 
 // One trajectory's propagation and crossing search with the group's shared
 // scratch vectors A, B and U (u_m at U + (m - 1) NP).
-template <class Ar, int G, int R>
+template <class Ar, int G, int R, bool DENSE = false>
 struct Expo {
     using cplx = typename Ar::cplx;
     static constexpr int NP = G * R;
@@ -128,12 +128,80 @@ struct Expo {
         return Ar::rval(Ar::rsum(g, nn));
     }
 
-    // out = P_l x, synchronised; returns ||out||^2
-    __device__ double apply_level(int l, const cplx *x, cplx *out)
+    // dst = x + s (M src) (x given) or s (M src) on the lane's rows, no
+    // synchronisation: the M product of the Taylor remainder and of the
+    // crossing's u_m (out of line for double-float, like level_part)
+    __device__ __forceinline__ void m_times(const cplx *src, cplx *dst, typename Ar::coef s, const cplx *x) const
+    {
+        if constexpr (Ar::kId == ArDF::kId)
+            m_times_ool(src, dst, s, x);
+        else
+            m_times_inl(src, dst, s, x);
+    }
+    __device__ __noinline__ void m_times_ool(const cplx *src, cplx *dst, typename Ar::coef s, const cplx *x) const
+    {
+        m_times_inl(src, dst, s, x);
+    }
+    __device__ __forceinline__ void m_times_inl(const cplx *src, cplx *dst, typename Ar::coef s, const cplx *x) const
+    {
+        if constexpr (DENSE) {  // the dense FP32 copy of M, when it has one
+            if (a.dense_off[0] >= 0) {
+                cpx<float> v[R];
+                dense_rows_f32<G, R>(a.dense + a.dense_off[0], a.dense_ld, src, g.gl, a.n, v);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int row = g.gl + G * r;
+                    if (row < a.n) {
+                        typename Ar::acc acc = Ar::zero();
+                        Ar::axpy(acc, s, v[r]);
+                        dst[row] = x ? Ar::add_scaled(x[row], Ar::coef_of(1.0), acc) : Ar::get(acc);
+                    }
+                }
+                return;
+            }
+        }
+#pragma unroll 1
+        for (int r = 0; r < R; ++r) {
+            const cplx mv = spmv_row<Ar, G>(M, src, g.gl, r);
+            const int row = g.gl + G * r;
+            if (row < a.n) {
+                typename Ar::acc acc = Ar::zero();
+                Ar::axpy(acc, s, mv);
+                dst[row] = x ? Ar::add_scaled(x[row], Ar::coef_of(1.0), acc) : Ar::get(acc);
+            }
+        }
+    }
+
+    // out = P_l x on the lane's rows; returns the lane's part of ||out||^2 (no
+    // synchronisation).  Double-float: out of line, so every propagation,
+    // descent and bracket check runs one copy of the product loop, which keeps
+    // the kernel's hot code inside the instruction cache (inlined at each call
+    // site, the long double-float copies evicted one another: instruction-fetch
+    // stalls were the largest stall; +23 % on Jaynes-Cummings).  The shorter
+    // FP32 and FP64 loops stay inline (out of line measured 3-12 % slower in
+    // complex64).
+    __device__ __forceinline__ typename Ar::red level_part_inl(int l, const cplx *x, cplx *out) const
     {
         typename Ar::red p[1];
         level_apply<Ar, G, R, 1>(level(l), x, out, g.gl, a.n, p);
-        const double nn = Ar::rval(Ar::rsum(g, p[0]));
+        return p[0];
+    }
+    __device__ __noinline__ typename Ar::red level_part_ool(int l, const cplx *x, cplx *out) const
+    {
+        return level_part_inl(l, x, out);
+    }
+    __device__ __forceinline__ typename Ar::red level_part(int l, const cplx *x, cplx *out) const
+    {
+        if constexpr (Ar::kId == ArDF::kId)
+            return level_part_ool(l, x, out);
+        else
+            return level_part_inl(l, x, out);
+    }
+
+    // out = P_l x, synchronised; returns ||out||^2
+    __device__ double apply_level(int l, const cplx *x, cplx *out)
+    {
+        const double nn = Ar::rval(Ar::rsum(g, level_part(l, x, out)));
         g.sync();
         ++n_rhs;
         return nn;
@@ -148,17 +216,7 @@ struct Expo {
         const typename Ar::coef sc = Ar::coef_of(s);
 #pragma unroll 1
         for (int m = kExpoTaylor; m >= 1; --m) {
-            const typename Ar::coef sm = Ar::cmul(sc, inv[m]);
-#pragma unroll 1
-            for (int r = 0; r < R; ++r) {
-                const cplx mv = spmv_row<Ar, G>(M, src, g.gl, r);
-                const int row = g.gl + G * r;
-                if (row < a.n) {
-                    typename Ar::acc acc = Ar::zero();
-                    Ar::axpy(acc, sm, mv);
-                    dst[row] = Ar::add_scaled(x[row], Ar::coef_of(1.0), acc);
-                }
-            }
+            m_times(src, dst, Ar::cmul(sc, inv[m]), x);
             g.sync();
             ++n_rhs;
             src = dst;
@@ -298,17 +356,7 @@ struct Expo {
 #pragma unroll 1
         for (int m = 1; m <= kExpoTaylor; ++m) {
             cplx *um = u(m);
-            const typename Ar::coef im = inv[m];
-#pragma unroll 1
-            for (int r2 = 0; r2 < R; ++r2) {
-                const cplx mv = spmv_row<Ar, G>(M, prev, g.gl, r2);
-                const int row = g.gl + G * r2;
-                if (row < a.n) {
-                    typename Ar::acc acc = Ar::zero();
-                    Ar::axpy(acc, im, mv);
-                    um[row] = Ar::get(acc);
-                }
-            }
+            m_times(prev, um, inv[m], nullptr);
             g.sync();
             ++n_rhs;
             prev = um;
@@ -459,6 +507,82 @@ struct ExpoTraj {
     unsigned long long n_jump;
 };
 
+// The rest of output interval j of trajectory il (Algorithm 1 (B)-(D) inside the
+// interval, then the outputs at t_j), given y = exp(M (t_j - x.t)) psi and
+// nn = ||y||^2: every crossing of the threshold is found, the jump applied and
+// the state propagated on to t_j.  Returns true with psi = psi(t_j) (x.t = t_j,
+// x.nb its squared norm), or false with x.status set (x.jdone = j).
+template <class Ar, int G, int R, int FEAT, bool DENSE = false>
+__device__ bool expo_interval(const KernelArgs &a, const Group<G> &g, const int *si, const typename Ar::real *sv,
+                              Expo<Ar, G, R, DENSE> &E, ExpoTraj &x, typename Ar::cplx *psi, typename Ar::cplx *y,
+                              double nn, int j, long long il, ExpoProp *PS, unsigned long long &n_acc)
+{
+    constexpr bool PROP = (FEAT & kFeatProposal) != 0;
+    using cplx = typename Ar::cplx;
+    const int gl = g.gl;
+    for (;;) {
+        if (!isfinite(nn)) {
+            x.status = 6;
+            break;
+        }
+        if (nn >= x.r) break;
+        if (++x.steps > a.max_steps) {
+            x.status = 4;
+            break;
+        }
+        // (B): the norm reaches r inside (x.t, t_j]
+        cplx *ytau = nullptr;
+        const double d = a.t[j] - x.t;
+        double s_hat = -1.0;
+        float *rec = nullptr;
+        if constexpr (PROP) s_hat = expo_predict<G>(a, g, PS, x.nb, nn, d, x.r, x.n_jump, il, &rec);
+        const double s = E.crossing(d, psi, x.nb, x.r, x.t, &ytau, s_hat);
+        if constexpr (PROP)
+            if (rec) rec[7] = (float)s;
+        double tau = x.t + s;
+        if (tau > a.t[j]) tau = a.t[j];
+        // (C)
+        const int ch = apply_jump<Ar, G, R, DENSE>(a, g, si, sv, psi, E.u(1), ytau, x.c);
+        if (ch < 0) {
+            x.status = 7;
+            break;
+        }
+        g.sync();
+        if (gl == 0 && (long long)x.n_jump < a.max_jumps) {
+            a.jump_t[(size_t)il * a.max_jumps + x.n_jump] = tau;
+            a.jump_ch[(size_t)il * a.max_jumps + x.n_jump] = ch;
+        }
+        ++x.n_jump;
+        ++n_acc;
+        // (D), then on to t_j
+        ++x.k;
+        jump_draws(a.seed, a.traj0 + il, x.k, x.r, x.c);
+        x.t = tau;
+        x.nb = 1.0;
+        if constexpr (PROP)
+            if (gl == 0) PS->gam_prev = -1.f;
+        y = E.propagate(a.t[j] - tau, psi);
+        nn = E.norm2(y);
+    }
+    if (x.status != 0) {
+        x.jdone = j;
+        return false;
+    }
+    if constexpr (PROP)  // the decay rate over this (jump-free) stretch, for the next crossing's features
+        if (gl == 0) PS->gam_prev = __logf((float)x.nb / (float)nn) / (float)(a.t[j] - x.t);
+    record_outputs<Ar, G, R>(a, g, si, sv, y, j, a.out + (size_t)il * a.n_t * a.n_obs, PROP ? PS->f + 4 : nullptr);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int row = gl + G * r;
+        if (row < a.n) psi[row] = y[row];
+    }
+    g.sync();
+    x.nb = nn;
+    x.t = a.t[j];
+    ++n_acc;
+    return true;
+}
+
 // Trajectories il0 .. il0 + live - 1 (live <= T) of the launch, in lock step.
 template <class Ar, int G, int R, int T, int FEAT>
 __device__ void run_group_expo(const KernelArgs &a, const Group<G> &g, const int *si, const typename Ar::real *sv,
@@ -512,7 +636,10 @@ __device__ void run_group_expo(const KernelArgs &a, const Group<G> &g, const int
     for (int j = 1; j < a.n_t; ++j) {
         typename Ar::red part[T];
         if (a.expo_uniform) {
-            level_apply<Ar, G, R, T>(E.level(a.expo_levels - 1), psi_all, y_all, gl, n, part);
+            if constexpr (T == 1)
+                part[0] = E.level_part(a.expo_levels - 1, psi_all, y_all);
+            else
+                level_apply<Ar, G, R, T>(E.level(a.expo_levels - 1), psi_all, y_all, gl, n, part);
             g.sync();
         }
         bool any = false;
@@ -537,67 +664,7 @@ __device__ void run_group_expo(const KernelArgs &a, const Group<G> &g, const int
                 y = E.propagate(a.t[j] - x.t, psi);
                 nn = E.norm2(y);
             }
-            for (;;) {
-                if (!isfinite(nn)) {
-                    x.status = 6;
-                    break;
-                }
-                if (nn >= x.r) break;
-                if (++x.steps > a.max_steps) {
-                    x.status = 4;
-                    break;
-                }
-                // (B): the norm reaches r inside (x.t, t_j]
-                cplx *ytau = nullptr;
-                const double d = a.t[j] - x.t;
-                double s_hat = -1.0;
-                float *rec = nullptr;
-                if constexpr (PROP) s_hat = expo_predict<G>(a, g, PS, x.nb, nn, d, x.r, x.n_jump, il0 + t, &rec);
-                const double s = E.crossing(d, psi, x.nb, x.r, x.t, &ytau, s_hat);
-                if constexpr (PROP)
-                    if (rec) rec[7] = (float)s;
-                double tau = x.t + s;
-                if (tau > a.t[j]) tau = a.t[j];
-                // (C)
-                const int ch = apply_jump<Ar, G, R>(a, g, si, sv, psi, E.u(1), ytau, x.c);
-                if (ch < 0) {
-                    x.status = 7;
-                    break;
-                }
-                g.sync();
-                if (gl == 0 && (long long)x.n_jump < a.max_jumps) {
-                    a.jump_t[(size_t)(il0 + t) * a.max_jumps + x.n_jump] = tau;
-                    a.jump_ch[(size_t)(il0 + t) * a.max_jumps + x.n_jump] = ch;
-                }
-                ++x.n_jump;
-                ++n_acc;
-                // (D), then on to t_j
-                ++x.k;
-                jump_draws(a.seed, a.traj0 + il0 + t, x.k, x.r, x.c);
-                x.t = tau;
-                x.nb = 1.0;
-                if constexpr (PROP)
-                    if (gl == 0) PS->gam_prev = -1.f;
-                y = E.propagate(a.t[j] - tau, psi);
-                nn = E.norm2(y);
-            }
-            if (x.status != 0) {
-                x.jdone = j;
-                continue;
-            }
-            if constexpr (PROP)  // the decay rate over this (jump-free) stretch, for the next crossing's features
-                if (gl == 0) PS->gam_prev = __logf((float)x.nb / (float)nn) / (float)(a.t[j] - x.t);
-            record_outputs<Ar, G, R>(a, g, si, sv, y, j, a.out + (size_t)(il0 + t) * a.n_t * a.n_obs,
-                                     PROP ? PS->f + 4 : nullptr);
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int row = gl + G * r;
-                if (row < n) psi[row] = y[row];
-            }
-            g.sync();
-            x.nb = nn;
-            x.t = a.t[j];
-            ++n_acc;
+            expo_interval<Ar, G, R, FEAT>(a, g, si, sv, E, x, psi, y, nn, j, il0 + t, PS, n_acc);
         }
         if (!any) break;
     }
@@ -760,6 +827,240 @@ cudaError_t launch_expo_prop(const KernelArgs &a, cudaStream_t stream, LaunchInf
     if (a.G == 16 && a.R == 4) return launch_expo_instance<Ar, 16, 4, F>(a, stream, info);
     if (a.G == 32 && a.R == 4) return launch_expo_instance<Ar, 32, 4, F>(a, stream, info);
     return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Lock-step form (tensor-core products).  On a uniform output grid every output
+// interval starts with the same product P_L psi, so all trajectories of a run
+// advance together: one launch of the tensor-core engine forms (P_L - I) psi for
+// every column (a GEMM; y = psi + that, added here in FP32), then this kernel
+// finishes interval lock_j of every column with the code above -- outputs, or
+// the crossing search, the jump and the propagation to t_j on the ladder -- one
+// group per column.  Complex64 arithmetic (FP32 state and propagators,
+// double-float norms); the operators are read from device memory (L1/L2), so
+// every layout fits, dense ones (M, C_n) from their column-major FP32 copies:
+// the packed form of a dense operator, read row by row from L2 with one
+// dependent load chain per entry, made each crossing take milliseconds.
+// ---------------------------------------------------------------------------
+
+struct LockCol {
+    ExpoTraj x;
+    unsigned long long n_acc, n_rhs, n_rej;
+    int root_iters;
+    int jdef;  // >= 0: the crossing found in interval jdef waits for the catch-up (psi still at t_{jdef-1})
+};
+static_assert(sizeof(LockCol) == kLockColBytes, "lock-step column record");
+
+// One group's column il in the three modes of the lock-step launch sequence:
+//   kLockInterval  interval lock_j (0: start): y = psi + (P_L - I) psi from the
+//                  tensor cores; without a crossing in the interval the outputs
+//                  at t_j, psi <- y; with one the column is deferred (appended to
+//                  the catch-up list, psi kept at t_{j-1})
+//   kLockCatchUp   a deferred column (taken from the list): its crossing search,
+//                  jump and propagation, then the intervals up to lock_j with the
+//                  ladder's P_L (SIMT), so it rejoins the lock step
+//   kLockFinish    the column's totals, jump count and failure outputs
+template <int G, int R>
+__device__ void lockstep_column(const KernelArgs &a, const Group<G> &g, const int *si, const ArF32::real *sv,
+                                const ArF32::coef *inv, ArF32::cplx *slots, long long il)
+{
+    using Ar = ArF32;
+    using cplx = Ar::cplx;
+    using S = ExpoSlots<1>;
+    constexpr int NP = G * R;
+    cplx *psi = slots + S::kPsi * NP, *ybuf = slots + S::kY * NP;
+    const int n = a.n, gl = g.gl, j = a.lock_j, half = a.lock_ld / 2;
+    LockCol *lc = static_cast<LockCol *>(a.lock_col) + il;
+    float *gpsi = a.lock_psi + (size_t)il * a.lock_ld;
+    Expo<Ar, G, R, true> E{a, g, csr_view<Ar>(a.op[0], si, sv), slots + S::kA * NP, slots + S::kB * NP,
+                           slots + S::kU * NP, inv};
+    ExpoTraj x;
+    int jdef = -1;
+    unsigned long long n_acc = 0;
+    bool write_psi = false;
+    if (a.lock_mode == kLockFinish) {
+        if (gl == 0) {
+            const LockCol c = *lc;
+            if (c.x.status != 0) {
+                double *out = a.out + (size_t)il * a.n_t * a.n_obs;
+                for (int jj = c.x.jdone; jj < a.n_t; ++jj)
+                    for (int q = 0; q < a.n_obs; ++q)
+                        out[(size_t)jj * a.n_obs + q] = __longlong_as_double(0x7ff8000000000000LL);
+                atomicCAS(a.first_error, 0, c.x.status);
+                atomicAdd(&a.counters[kFailed], 1ULL);
+            }
+            if (a.max_jumps > 0) a.n_jumps[il] = (int)c.x.n_jump;
+            atomicAdd(&a.counters[kAccepted], c.n_acc);
+            atomicAdd(&a.counters[kRejected], c.n_rej);
+            atomicAdd(&a.counters[kRhs], c.n_rhs);
+            atomicAdd(&a.counters[kJumps], c.x.n_jump);
+            atomicAdd(&a.counters[kRootIters], (unsigned long long)c.root_iters);
+        }
+        return;
+    }
+    if (a.lock_mode == kLockInterval && j == 0) {
+        // (A): psi0, the first draws, output 0
+        const cplx *psi0 = static_cast<const cplx *>(a.psi0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int row = gl + G * r;
+            if (row < n) psi[row] = psi0[row];
+        }
+        g.sync();
+        x.k = 0;
+        jump_draws(a.seed, a.traj0 + il, 0, x.r, x.c);
+        x.t = a.t[0];
+        x.steps = 0;
+        x.status = 0;
+        x.jdone = a.n_t;
+        x.n_jump = 0;
+        record_outputs<Ar, G, R>(a, g, si, sv, psi, 0, a.out + (size_t)il * a.n_t * a.n_obs, nullptr);
+        x.nb = E.norm2(psi);
+        write_psi = true;
+    } else {
+        x = lc->x;
+        jdef = lc->jdef;
+        if (x.status != 0) return;
+        if (a.lock_mode == kLockInterval) {
+            if (jdef >= 0) return;  // waiting for the catch-up
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int row = gl + G * r;
+                if (row < n) {  // y = psi + (P_L - I) psi
+                    const float pr = gpsi[row], pi = gpsi[half + row];
+                    psi[row] = cplx{pr, pi};
+                    ybuf[row] = cplx{pr + a.lock_y[(size_t)il * a.lock_ld + row],
+                                     pi + a.lock_y[(size_t)il * a.lock_ld + half + row]};
+                }
+            }
+            g.sync();
+            ++E.n_rhs;  // the tensor cores' product
+            const double nn = E.norm2(ybuf);
+            if (nn < x.r) {  // a crossing: deferred to the catch-up
+                jdef = j;
+                if (gl == 0) a.lock_list[atomicAdd(&a.queue[0], 1ULL)] = (int)il;
+            } else {
+                ++x.steps;
+                write_psi = expo_interval<Ar, G, R, 0, true>(a, g, si, sv, E, x, psi, ybuf, nn, j, il, nullptr, n_acc);
+            }
+        } else {  // kLockCatchUp: intervals jdef .. lock_j on the ladder
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int row = gl + G * r;
+                if (row < n) psi[row] = cplx{gpsi[row], gpsi[half + row]};
+            }
+            g.sync();
+            bool ok = true;
+#pragma unroll 1
+            for (int jj = jdef; jj <= j && ok; ++jj) {
+                const double nn = E.apply_level(a.expo_levels - 1, psi, ybuf);
+                ++x.steps;
+                ok = expo_interval<Ar, G, R, 0, true>(a, g, si, sv, E, x, psi, ybuf, nn, jj, il, nullptr, n_acc);
+            }
+            jdef = -1;
+            write_psi = ok;
+        }
+    }
+    if (write_psi) {  // psi(t_j) back to its column
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int row = gl + G * r;
+            if (row < n) {
+                gpsi[row] = psi[row].re;
+                gpsi[half + row] = psi[row].im;
+            }
+        }
+    }
+    const bool fresh = a.lock_mode == kLockInterval && j == 0;
+    const unsigned long long acc_tot = n_acc + (fresh ? 0 : lc->n_acc);
+    const unsigned long long rhs_tot = E.n_rhs + (fresh ? 0 : lc->n_rhs);
+    const unsigned long long rej_tot = E.n_rej + (fresh ? 0 : lc->n_rej);
+    const int root_tot = E.root_iters + (fresh ? 0 : lc->root_iters);
+    g.sync();  // every lane has read the record before lane 0 rewrites it
+    if (gl == 0) {
+        lc->x = x;
+        lc->jdef = jdef;
+        lc->n_acc = acc_tot;
+        lc->n_rhs = rhs_tot;
+        lc->n_rej = rej_tot;
+        lc->root_iters = root_tot;
+    }
+}
+
+template <int G, int R, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 2)) mcwf_expo_lockstep_kernel(const __grid_constant__ KernelArgs a)
+{
+    using Ar = ArF32;
+    using cplx = Ar::cplx;
+    using real = Ar::real;
+    constexpr int NP = G * R;
+    constexpr int GROUPS = BLOCK / G;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int *si = a.ints;
+    const real *sv = static_cast<const real *>(a.vals);
+    Ar::coef *inv = reinterpret_cast<Ar::coef *>(smem + a.smem_coef_offset);
+    if (threadIdx.x <= kExpoTaylor) inv[threadIdx.x] = Ar::coef_of(threadIdx.x ? 1.0 / threadIdx.x : 0.0);
+    __syncthreads();
+    const Group<G> g(threadIdx.x, reinterpret_cast<unsigned long long *>(smem + a.smem_scratch_offset));
+    cplx *slots = reinterpret_cast<cplx *>(smem + a.smem_ybuf_offset) +
+                  (size_t)(threadIdx.x / G) * ExpoSlots<1>::kCount * NP;
+    if (a.lock_mode == kLockCatchUp) {
+        // the deferred columns, one at a time per group from the shared list
+        const long long count = (long long)a.queue[0];
+        for (;;) {
+            unsigned long long i = 0;
+            if (g.gl == 0) i = atomicAdd(&a.queue[1], 1ULL);
+            i = g.bcast0(i);
+            if ((long long)i >= count) break;
+            lockstep_column<G, R>(a, g, si, sv, inv, slots, (long long)a.lock_list[i]);
+            g.sync();
+        }
+        return;
+    }
+    for (long long il = (long long)blockIdx.x * GROUPS + threadIdx.x / G; il < a.ntraj;
+         il += (long long)gridDim.x * GROUPS) {
+        lockstep_column<G, R>(a, g, si, sv, inv, slots, il);
+        g.sync();
+    }
+}
+
+template <int G, int R>
+cudaError_t launch_expo_lockstep_instance(const KernelArgs &a0, cudaStream_t stream, LaunchInfo *info)
+{
+    using cplx = ArF32::cplx;
+    constexpr int BLOCK = block_for_group<G>();
+    constexpr int GROUPS = BLOCK / G;
+    KernelArgs a = a0;
+    auto al16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    const size_t sb = al16((size_t)GROUPS * (Group<G>::kWarps + 1) * 8);
+    const size_t cb = al16((kExpoTaylor + 1) * sizeof(ArF32::coef));
+    a.smem_vals_offset = 0;
+    a.smem_scratch_offset = 0;
+    a.smem_coef_offset = (int)sb;
+    a.smem_mlp_offset = (int)(sb + cb);
+    a.smem_ybuf_offset = (int)(sb + cb);
+    const size_t smem = sb + cb + (size_t)GROUPS * ExpoSlots<1>::kCount * G * R * sizeof(cplx);
+    if (smem > 227 * 1024 || a.lock_ld < 2 * a.n) return cudaErrorInvalidValue;
+    auto kern = mcwf_expo_lockstep_kernel<G, R, BLOCK>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, nb = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, BLOCK, smem)) != cudaSuccess) return e;
+    if (nb < 1) nb = 1;
+    const long long need = (a.ntraj + GROUPS - 1) / GROUPS;
+    long long grid = (long long)nb * sms;
+    if (need < grid) grid = need < 1 ? 1 : need;
+    kern<<<(unsigned)grid, BLOCK, smem, stream>>>(a);
+    if (info) {
+        info->group = G;
+        info->rows = R;
+        info->grid = (int)grid;
+        info->block = BLOCK;
+        info->smem = smem;
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace qtm

@@ -129,6 +129,51 @@ __device__ __forceinline__ void spmv_rows(const CsrView<Ar> &A, const typename A
     }
 }
 
+// v[r] = (D x)[gl + G r] for a dense complex64 operator D, column-major with
+// column stride ld: one column per iteration, the group's rows of a column in
+// consecutive lanes (coalesced loads), x_c broadcast from shared memory
+template <int G, int R>
+__device__ __forceinline__ void dense_rows_f32(const float2 *D, int ld, const cpx<float> *x, int gl, int n,
+                                               cpx<float> (&v)[R])
+{
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = cpx<float>{0.f, 0.f};
+    const float2 *col = D + gl;
+#pragma unroll 4
+    for (int c = 0; c < n; ++c) {
+        const cpx<float> xc = x[c];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (gl + G * r < n) {
+                const float2 m = col[G * r];
+                v[r].re = fmaf(m.x, xc.re, fmaf(-m.y, xc.im, v[r].re));
+                v[r].im = fmaf(m.x, xc.im, fmaf(m.y, xc.re, v[r].im));
+            }
+        }
+        col += ld;
+    }
+}
+
+// out = A_i x on the lane's rows (x synchronised): from the dense FP32 copy when
+// DENSE and the operator has one, else from the packed form
+template <class Ar, int G, int R, bool DENSE>
+__device__ __forceinline__ void op_rows(const KernelArgs &a, int i, const int *si, const typename Ar::real *sv,
+                                        const typename Ar::cplx *x, typename Ar::cplx *out, int gl)
+{
+    if constexpr (DENSE) {
+        static_assert(Ar::kId == 2, "dense operator copies are complex64");
+        if (a.dense_off[i] >= 0) {
+            cpx<float> v[R];
+            dense_rows_f32<G, R>(a.dense + a.dense_off[i], a.dense_ld, x, gl, a.n, v);
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (gl + G * r < a.n) out[gl + G * r] = v[r];
+            return;
+        }
+    }
+    spmv_rows<Ar, G, R>(csr_view<Ar>(a.op[i], si, sv), x, out, gl, a.n);
+}
+
 // dst = psi + h sum_j w_j K_j on the lane's rows (the continuous extension at theta)
 template <class Ar, int G, int R>
 __device__ __noinline__ void dense_rows(const Coefs<Ar> &C, const Lanes<Ar, G, R> &L, double h, double th,
@@ -420,7 +465,7 @@ __device__ __noinline__ double locate_crossing(const Coefs<Ar> &C, Lanes<Ar, G, 
 // vector (group synchronised).  Chooses the channel, writes C_n* y / ||C_n* y||
 // to psi (lane rows; tmp is lane-row scratch), and returns the channel (or -1
 // when every weight is zero).
-template <class Ar, int G, int R>
+template <class Ar, int G, int R, bool DENSE = false>
 __device__ __noinline__ int apply_jump(const KernelArgs &a, Group<G> g, const int *si,
                                        const typename Ar::real *sv, typename Ar::cplx *psi,
                                        typename Ar::cplx *tmp, const typename Ar::cplx *y, double ck)
@@ -429,7 +474,7 @@ __device__ __noinline__ int apply_jump(const KernelArgs &a, Group<G> g, const in
     double wq[kMaxChannels];
     double wsum = 0.0;
     for (int q = 0; q < a.n_c; ++q) {
-        spmv_rows<Ar, G, R>(csr_view<Ar>(a.op[1 + q], si, sv), y, tmp, gl, n);
+        op_rows<Ar, G, R, DENSE>(a, 1 + q, si, sv, y, tmp, gl);
         typename Ar::red part = Ar::rzero();
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -450,7 +495,7 @@ __device__ __noinline__ int apply_jump(const KernelArgs &a, Group<G> g, const in
             break;
         }
     }
-    spmv_rows<Ar, G, R>(csr_view<Ar>(a.op[1 + ch], si, sv), y, psi, gl, n);
+    op_rows<Ar, G, R, DENSE>(a, 1 + ch, si, sv, y, psi, gl);
     const double nc = sqrt(wq[ch]);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
@@ -1188,7 +1233,7 @@ __device__ void run_trajectory_krylov(const KernelArgs &a, const Group<G> &g, co
         krylov_step_coefs<Ar, G>(KC, KS, g, h * up);
 
         typename Ar::errt esum = 0;
-        typename Ar::red nr = Ar::rzero();
+        float nr32 = 0.f;  // ||ynew||^2 from the leading FP32 parts (the crossing pre-test)
         krylov_rows<G, R>([&](int r) {
             const int row = gl + G * r;
             if (row < n) {
@@ -1204,7 +1249,7 @@ __device__ void run_trajectory_krylov(const KernelArgs &a, const Group<G> &g, co
                 const float eim = fmaf(KS->ge[0], Ar::im32(w5),
                                        fmaf(KS->ge[1], Ar::im32(w6), KS->ge[2] * Ar::im32(w7)));
                 esum += krylov_err_term<Ar>(ere, eim, y0, y1, rtol, atol);
-                nr = Ar::radd(nr, Ar::abs2(y1));
+                nr32 = fmaf(Ar::re32(y1), Ar::re32(y1), fmaf(Ar::im32(y1), Ar::im32(y1), nr32));
             }
         });
         // error norm, acceptance and controller in FP32 (the double-float policy's choice)
@@ -1224,9 +1269,23 @@ __device__ void run_trajectory_krylov(const KernelArgs &a, const Group<G> &g, co
         }
         ++n_acc;
         const double t_new = last ? t_end : t + h;
-        const double nn = Ar::rval(Ar::rsum(g, nr));
+        // (B) crossing test ||ynew||^2 < r: decided from the FP32 sum when it lies
+        // outside r (1 +- 1e-4) -- its relative error is below 1e-6 (leading parts
+        // good to 2^-24, a dozen FP32 roundings of positive terms) -- else from the
+        // double-float norm, so the decision is the one the exact norm gives
+        const float s32 = g.sum(nr32), rkf = (float)rk;
+        bool crossed = s32 < 0.9999f * rkf;
+        if (!crossed && !(s32 > 1.0001f * rkf)) {
+            typename Ar::red nr = Ar::rzero();
+#pragma unroll 1
+            for (int r = 0; r < R; ++r) {
+                const int row = gl + G * r;
+                if (row < n) nr = Ar::radd(nr, Ar::abs2(yn[row]));
+            }
+            crossed = Ar::rval(Ar::rsum(g, nr)) < rk;
+        }
 
-        if (nn < rk) {
+        if (crossed) {
             // (C): the norm reached r inside this step
             const double th = krylov_crossing<Ar, G, R>(KC, KS, L, g, rk, root_iters);
             double tau = t + th * h;

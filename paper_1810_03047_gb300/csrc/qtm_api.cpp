@@ -96,8 +96,15 @@ struct qtm_ctx {
     int expo_levels = 0, expo_uniform = 0;
     double expo_delta = 0.0;
     DevBuf d_expo;
+    // the exponential method on the tensor cores (QTM_PREC_BF16X6, uniform grid):
+    // bf16 splits of the real form of P_L - I and their tensor map; the lock-step
+    // columns' states, products, records and deferred list
+    DevBuf d_op_expo, d_lpsi, d_ly, d_lcol, d_llist;
+    CUtensorMap expo_map{};
     long long last_ntraj = -1;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};  // kernel start, kernel end, reduction end
+    // kernel start, kernel end, reduction end; one tensor-core product's start and end
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    bool product_timed = false;
     bool timed = false;
     LaunchInfo info{};
     std::string err;
@@ -494,7 +501,8 @@ void destroy_ctx(qtm_ctx *ctx)
                       &ctx->d_moments, &ctx->d_scale, &ctx->d_njumps, &ctx->d_jump_t, &ctx->d_jump_ch,
                       &ctx->d_rec, &ctx->d_mlp, &ctx->d_X, &ctx->d_T, &ctx->d_gpart, &ctx->d_lpart,
                       &ctx->d_grad, &ctx->d_loss, &ctx->d_m, &ctx->d_v, &ctx->d_op, &ctx->d_state,
-                      &ctx->d_col, &ctx->d_rhs, &ctx->d_dense, &ctx->d_expo};
+                      &ctx->d_col, &ctx->d_rhs, &ctx->d_dense, &ctx->d_expo, &ctx->d_op_expo, &ctx->d_lpsi,
+                      &ctx->d_ly, &ctx->d_lcol, &ctx->d_llist};
     for (DevBuf *b : bufs) dev_free(ctx, *b);
     cudaStreamSynchronize(ctx->stream);
     for (cudaEvent_t &e : ctx->ev)
@@ -535,6 +543,8 @@ float bf16_value(uint16_t b)
 // out = [x0 rows][x1 rows][x2 rows].
 // The engine's operator: the real form of 2^-shift M (the Krylov form's scaled
 // operator; scaling by a power of two is exact), split into three bf16 terms.
+std::vector<uint16_t> tc_split(const std::vector<double> &mr);
+
 std::vector<uint16_t> tc_operator(const Csr &M, int np, int shift)
 {
     const int kd = 2 * np;
@@ -549,6 +559,29 @@ std::vector<uint16_t> tc_operator(const Csr &M, int np, int shift)
             mr[(size_t)(np + i) * kd + k] = im;
             mr[(size_t)(np + i) * kd + np + k] = re;
         }
+    return tc_split(mr);
+}
+
+// The same real form and split for a dense n x n complex matrix (row-major): the
+// exponential method's top-level propagator minus the identity.
+std::vector<uint16_t> tc_operator_dense(const cd *P, int n, int np)
+{
+    const int kd = 2 * np;
+    std::vector<double> mr((size_t)kd * kd, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int k = 0; k < n; ++k) {
+            const double re = P[(size_t)i * n + k].real(), im = P[(size_t)i * n + k].imag();
+            mr[(size_t)i * kd + k] = re;
+            mr[(size_t)i * kd + np + k] = -im;
+            mr[(size_t)(np + i) * kd + k] = im;
+            mr[(size_t)(np + i) * kd + np + k] = re;
+        }
+    return tc_split(mr);
+}
+
+// [x0 rows][x1 rows][x2 rows] of the three-term bf16 split of mr
+std::vector<uint16_t> tc_split(const std::vector<double> &mr)
+{
     std::vector<uint16_t> out(3 * mr.size());
     for (size_t i = 0; i < mr.size(); ++i) {
         double r = mr[i];
@@ -567,7 +600,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
 
 // Tensor map over the operator splits [3 kd rows][kd] bf16: boxes of 64 (one
 // 128-byte row) x 128 rows with the 128-byte swizzle the MMA descriptors expect.
-qtm_status tc_make_map(qtm_ctx *ctx)
+qtm_status tc_make_map(qtm_ctx *ctx, void *base, CUtensorMap *map)
 {
     void *fn = nullptr;
     cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
@@ -580,7 +613,7 @@ qtm_status tc_make_map(qtm_ctx *ctx)
     const cuuint64_t strides[1] = {(cuuint64_t)kd * 2};
     const cuuint32_t box[2] = {64, 128};
     const cuuint32_t estr[2] = {1, 1};
-    const CUresult r = ((EncodeTiledFn)fn)(&ctx->op_map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, ctx->d_op.p, dims,
+    const CUresult r = ((EncodeTiledFn)fn)(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims,
                                            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -640,7 +673,7 @@ qtm_status tc_setup(qtm_ctx *ctx)
                                                 cudaMemcpyHostToDevice, ctx->stream))) ||
         (e = cudaStreamSynchronize(ctx->stream)))
         return cuda_fail(ctx, e, "qtm_create: tensor-core operator upload");
-    return tc_make_map(ctx);
+    return tc_make_map(ctx, ctx->d_op.p, &ctx->op_map);
 }
 
 }  // namespace
@@ -863,7 +896,13 @@ static qtm_status reserve_run(qtm_ctx *ctx, int64_t ntraj)
         (e = dev_reserve(ctx, ctx->d_partial, qtm::kMomentWords * (size_t)S * P * sizeof(long long))) ||
         (e = dev_reserve(ctx, ctx->d_moments, qtm::kMomentWords * P * sizeof(long long))))
         return cuda_fail(ctx, e, "qtm_run: device allocation");
-    if (ctx->precision == QTM_PREC_BF16X6 && ntraj > 0) {
+    if (ctx->precision == QTM_PREC_BF16X6 && ctx->method == QTM_METHOD_EXPONENTIAL && ntraj > 0) {
+        const size_t vb = (size_t)ntraj * 2 * ctx->np * sizeof(float);
+        if ((e = dev_reserve(ctx, ctx->d_lpsi, vb)) || (e = dev_reserve(ctx, ctx->d_ly, vb)) ||
+            (e = dev_reserve(ctx, ctx->d_lcol, (size_t)ntraj * qtm::kLockColBytes)) ||
+            (e = dev_reserve(ctx, ctx->d_llist, (size_t)ntraj * sizeof(int))))
+            return cuda_fail(ctx, e, "qtm_run: device allocation");
+    } else if (ctx->precision == QTM_PREC_BF16X6 && ntraj > 0) {
         const size_t cols = (size_t)qtm::dense_tc_ctas(ntraj, ctx->sms) * qtm::kTcCols;
         if ((e = dev_reserve(ctx, ctx->d_state, qtm::kNumDenseVecs * cols * 2 * ctx->np * sizeof(float))) ||
             (e = dev_reserve(ctx, ctx->d_col, cols * sizeof(qtm::DenseCol))))
@@ -938,7 +977,66 @@ static qtm_status enqueue_run(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64
         a.prop_margin = ctx->prop_margin;
         a.krylov_shift = ctx->krylov_shift;
         const bool prop = a.rec_stride > 0 || a.mlp != nullptr;
-        if (ctx->precision == QTM_PREC_BF16X6) {
+        if (ctx->precision == QTM_PREC_BF16X6 && ctx->method == QTM_METHOD_EXPONENTIAL) {
+            if (prop) return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_run: no learned proposal on the tensor-core path");
+            // lock-step exponential method: interval 0 starts every column; then
+            // per output interval the tensor cores form (P_L - I) psi for all
+            // columns and the per-interval kernel finishes each column's interval
+            a.expo = ctx->d_expo.p;
+            a.expo_levels = ctx->expo_levels;
+            a.expo_uniform = 1;
+            a.expo_delta = ctx->expo_delta;
+            a.lock_psi = (float *)ctx->d_lpsi.p;
+            a.lock_y = (const float *)ctx->d_ly.p;
+            a.lock_col = ctx->d_lcol.p;
+            a.lock_ld = 2 * ctx->np;
+            a.lock_list = (int *)ctx->d_llist.p;
+            a.dense = (const float2 *)ctx->d_dense.p;
+            a.dense_ld = ctx->np;
+            for (int i = 0; i < qtm::kMaxOps; ++i)
+                a.dense_off[i] = i < (int)ctx->dense_off.size() && ctx->dense_off[i] >= 0 ? ctx->dense_off[i] : -1;
+            qtm::DenseArgs d{};
+            d.k = a;
+            d.np = ctx->np;
+            d.mode = qtm::kDenseRhs;
+            d.wait_limit_ns = ctx->wait_limit_ns;
+            d.rhs_in = (const float *)ctx->d_lpsi.p;
+            d.rhs_out = (float *)ctx->d_ly.p;
+            d.rhs_n = ntraj;
+            qtm::LaunchInfo tc_info{};
+            // a column whose norm crosses its threshold inside an interval leaves
+            // the lock step until the next catch-up launch (every kCatchUpEvery
+            // intervals and after the last), which resolves the deferred columns
+            // with every group of the GPU working through the list, instead of
+            // each interval waiting for its slowest crossing
+            constexpr int kCatchUpEvery = 8;
+            ctx->product_timed = with_events && ctx->n_t > 1;
+            auto lockstep = [&](int mode, int j) -> qtm_status {
+                a.lock_mode = mode;
+                a.lock_j = j;
+                const cudaError_t le = qtm::launch_expo_lockstep(a, s, &ctx->info);
+                if (le == cudaErrorInvalidValue)
+                    return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_run: no lock-step kernel fits this problem");
+                if (le != cudaSuccess) return cuda_fail(ctx, le, "qtm_run: lock-step kernel launch");
+                return QTM_OK;
+            };
+            qtm_status ls;
+            for (int j = 0; j < ctx->n_t; ++j) {
+                if (j == 1 && with_events && (e = cudaEventRecord(ctx->ev[3], s)) != cudaSuccess)
+                    return cuda_fail(ctx, e, "qtm_run: cudaEventRecord");
+                if (j > 0 && (e = qtm::launch_dense_tc(d, ctx->expo_map, s, &tc_info)) != cudaSuccess)
+                    return cuda_fail(ctx, e, "qtm_run: tensor-core product launch");
+                if (j == 1 && with_events && (e = cudaEventRecord(ctx->ev[4], s)) != cudaSuccess)
+                    return cuda_fail(ctx, e, "qtm_run: cudaEventRecord");
+                if ((ls = lockstep(qtm::kLockInterval, j))) return ls;
+                if (j > 0 && (j % kCatchUpEvery == 0 || j == ctx->n_t - 1)) {
+                    if ((ls = lockstep(qtm::kLockCatchUp, j))) return ls;
+                    if ((e = cudaMemsetAsync(ctx->d_queue.p, 0, 16, s)) != cudaSuccess)
+                        return cuda_fail(ctx, e, "qtm_run: cudaMemsetAsync");
+                }
+            }
+            if ((ls = lockstep(qtm::kLockFinish, 0))) return ls;
+        } else if (ctx->precision == QTM_PREC_BF16X6) {
             if (prop) return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_run: no learned proposal on the tensor-core path");
             qtm::DenseArgs d{};
             d.k = a;
@@ -1376,6 +1474,9 @@ qtm_status qtm_stats(qtm_ctx *ctx, qtm_stats_t *out)
         if (ctx->last_ntraj > 0 && cudaEventElapsedTime(&ms, ctx->ev[0], ctx->ev[1]) == cudaSuccess)
             out->kernel_ms = ms;
         if (cudaEventElapsedTime(&ms, ctx->ev[1], ctx->ev[2]) == cudaSuccess) out->reduce_ms = ms;
+        if (ctx->product_timed && ctx->method == QTM_METHOD_EXPONENTIAL && ctx->precision == QTM_PREC_BF16X6 &&
+            cudaEventElapsedTime(&ms, ctx->ev[3], ctx->ev[4]) == cudaSuccess)
+            out->product_ms = ms;
     }
     return QTM_OK;
 }
@@ -1724,13 +1825,18 @@ qtm_status qtm_set_method(qtm_ctx *ctx, int32_t method)
     if (!ctx) return fail(nullptr, QTM_ERR_ARG, "qtm_set_method: ctx is NULL");
     ctx->err.clear();
     if (method == QTM_METHOD_DOPRI5) {
+        if (ctx->precision == QTM_PREC_BF16X6 && ctx->method == QTM_METHOD_EXPONENTIAL) {
+            // back to the Dormand-Prince engine's packing: one lane per row group of 32
+            ctx->method = QTM_METHOD_DOPRI5;
+            repack(ctx, qtm::Layout{32, ctx->np / 32});
+            qtm_status st = upload_ops(ctx);
+            if (st) return st;
+        }
         ctx->method = QTM_METHOD_DOPRI5;
         ctx->last_ntraj = -1;
         return QTM_OK;
     }
     if (method != QTM_METHOD_EXPONENTIAL) return fail(ctx, QTM_ERR_ARG, "qtm_set_method: unknown method");
-    if (ctx->precision == QTM_PREC_BF16X6)
-        return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_set_method: the tensor-core engine integrates with Dormand-Prince");
     if (!ctx->Dops.empty())
         return fail(ctx, QTM_ERR_UNSUPPORTED, "qtm_set_method: the exponential method takes a constant Hamiltonian");
     if (ctx->n > qtm::kMaxDimExpo) {
@@ -1752,6 +1858,9 @@ qtm_status qtm_set_method(qtm_ctx *ctx, int32_t method)
         }
         span = uniform ? mean : gmax;
     }
+    if (ctx->precision == QTM_PREC_BF16X6 && ctx->n_t > 1 && !uniform)
+        return fail(ctx, QTM_ERR_UNSUPPORTED,
+                    "qtm_set_method: the exponential method on the tensor cores needs a uniform output grid");
     std::vector<cd> ladder;
     double delta = 0.0;
     const int levels = expm_ladder(ctx->M, span, ladder, delta);
@@ -1760,11 +1869,43 @@ qtm_status qtm_set_method(qtm_ctx *ctx, int32_t method)
     ctx->expo_levels = levels;
     ctx->expo_uniform = uniform;
     ctx->expo_delta = delta;
+    const int was = ctx->method;
     ctx->method = QTM_METHOD_EXPONENTIAL;
-    qtm_status st = upload_ladder(ctx);
-    if (st) {
-        ctx->method = QTM_METHOD_DOPRI5;
-        return st;
+    qtm_status st;
+    if (ctx->precision == QTM_PREC_BF16X6) {
+        // the per-interval kernel's lane layout (its groups read the operators and
+        // the ladder from device memory), and for the tensor cores the bf16 splits
+        // of D = P_L - I: the per-interval kernel forms y = psi + D psi in FP32 with
+        // rounding to nearest, so the tensor cores' accumulation error (several
+        // times that of an FP32 product, met once per interval by the state)
+        // scales with ||D|| ~ ||M dt|| instead of ||P_L|| ~ 1
+        const int n = ctx->n;
+        repack(ctx, n <= 64 ? qtm::Layout{32, 2} : n <= 128 ? qtm::Layout{64, 2} : qtm::Layout{128, 2});
+        st = upload_ops(ctx);  // operators and ladder
+        if (!st) {
+            std::vector<cd> D(ctx->ladder.begin() + (size_t)(levels - 1) * n * n,
+                              ctx->ladder.begin() + (size_t)levels * n * n);
+            for (int i = 0; i < n; ++i) D[(size_t)i * n + i] -= 1.0;
+            std::vector<uint16_t> op = tc_operator_dense(D.data(), n, ctx->np);
+            cudaError_t e;
+            if ((e = dev_reserve(ctx, ctx->d_op_expo, op.size() * sizeof(uint16_t))) ||
+                (e = cudaMemcpyAsync(ctx->d_op_expo.p, op.data(), op.size() * sizeof(uint16_t),
+                                     cudaMemcpyHostToDevice, ctx->stream)) ||
+                (e = cudaStreamSynchronize(ctx->stream)))
+                st = cuda_fail(ctx, e, "qtm_set_method: upload");
+            else
+                st = tc_make_map(ctx, ctx->d_op_expo.p, &ctx->expo_map);
+        }
+        if (st) {
+            qtm_set_method(ctx, QTM_METHOD_DOPRI5);  // repacks for the engine
+            return st;
+        }
+    } else {
+        st = upload_ladder(ctx);
+        if (st) {
+            ctx->method = was == QTM_METHOD_EXPONENTIAL ? QTM_METHOD_DOPRI5 : was;
+            return st;
+        }
     }
     ctx->last_ntraj = -1;
     return QTM_OK;

@@ -109,6 +109,22 @@ struct KernelArgs {
     // Krylov form of the Dormand-Prince step: 2^krylov_shift >= ||M|| (the
     // Krylov vectors are kept as (2^-krylov_shift M)^k psi)
     int krylov_shift;
+    // lock-step exponential method (tensor-core products, uniform grid): column il
+    // holds psi at lock_psi + il lock_ld (lock_ld / 2 real parts, then the
+    // imaginary parts), the tensor cores' product (P_L - I) psi at
+    // lock_y + il lock_ld, and its record at lock_col[il]
+    float *lock_psi;
+    const float *lock_y;
+    void *lock_col;
+    int lock_j, lock_ld;
+    int lock_mode;            // LockMode: interval lock_j, catch-up of the deferred columns, or finish
+    int *lock_list;           // [ntraj] deferred columns (count in queue[0], catch-up position in queue[1])
+    // FP32 copies of dense operators for the lock-step kernel's products
+    // (operator i in the order of op): dense_off[i] >= 0: column-major, column c
+    // at dense + dense_off[i] + c dense_ld; < 0: none (the packed form is used)
+    const float2 *dense;
+    int dense_ld;
+    int dense_off[kMaxOps];
 };
 
 enum CounterIndex { kAccepted = 0, kRejected, kRhs, kJumps, kRootIters, kFailed, kPropMiss, kNumCounters };
@@ -132,6 +148,15 @@ cudaError_t launch_mcwf_df64_small(const KernelArgs &args, cudaStream_t stream, 
 cudaError_t launch_mcwf_df64_large(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
 cudaError_t launch_mcwf_c64_small(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
 cudaError_t launch_mcwf_c64_large(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+// One launch of the lock-step exponential method (complex64 arithmetic on the
+// layouts 32 x 2, 64 x 2 and 128 x 2) in mode args.lock_mode: output interval
+// args.lock_j of columns 0 .. args.ntraj - 1, the catch-up of the deferred
+// columns to interval args.lock_j, or the final totals.  cudaErrorInvalidValue
+// for any other layout.
+cudaError_t launch_expo_lockstep(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
+// Record of one lock-step column (device layout; zeroed storage is not needed).
+constexpr int kLockColBytes = 96;
+enum LockMode { kLockInterval = 0, kLockCatchUp = 1, kLockFinish = 2 };
 // Instantiations with the learned proposal compiled in (single-warp layouts only).
 cudaError_t launch_mcwf_c128_prop(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);
 cudaError_t launch_mcwf_df64_prop(const KernelArgs &args, cudaStream_t stream, LaunchInfo *info);

@@ -85,7 +85,7 @@ class QtmStats(ct.Structure):
                 ("failed", ct.c_int64), ("first_error", ct.c_int32), ("kernel_group", ct.c_int32),
                 ("kernel_rows", ct.c_int32), ("grid", ct.c_int32), ("block", ct.c_int32),
                 ("reserved", ct.c_int32), ("kernel_ms", ct.c_double), ("reduce_ms", ct.c_double),
-                ("proposal_misses", ct.c_int64)]
+                ("proposal_misses", ct.c_int64), ("product_ms", ct.c_double)]
 
 
 ALLOC_FN = ct.CFUNCTYPE(ct.c_void_p, ct.c_size_t, ct.c_void_p, ct.c_void_p)

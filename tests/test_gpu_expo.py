@@ -160,11 +160,6 @@ def test_expo_switch_back_to_dopri5_is_bitwise_the_default():
 
 def test_expo_argument_errors():
     prob = S.purcell_qubit(ntraj=4)
-    ctx = Q.qtm_create(prob, precision=Q.QTM_PREC_BF16X6)
-    with pytest.raises(Q.QtmError) as ei:
-        Q.qtm_set_method(ctx, Q.QTM_METHOD_EXPONENTIAL)
-    assert ei.value.status == Q.QTM_ERR_UNSUPPORTED
-    Q.qtm_destroy(ctx)
     ctx = Q.qtm_create(prob)
     with pytest.raises(Q.QtmError) as ei:
         Q.qtm_set_method(ctx, 7)
