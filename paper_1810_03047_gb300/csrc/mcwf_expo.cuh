@@ -36,7 +36,15 @@
 
 namespace qtm {
 
-constexpr int kExpoTaylor = 9;  // degree of the Taylor polynomial of exp(s M), s <= delta
+constexpr int kExpoTaylor = 9;  // largest degree of the Taylor polynomial of exp(s M), s <= delta
+
+// The degree used by an arithmetic.  The ladder's delta keeps ||s M|| <= 1/16, so
+// the truncation is below (1/16)^(K+1) / (K+1)!: 2.4e-19 at K = 9 for the
+// FP64-class arithmetics, 8.3e-11 at K = 5 -- far below FP32 rounding -- for
+// complex64, whose crossing search and remainders thus take four products
+// fewer each.
+template <class Ar>
+__host__ __device__ constexpr int expo_degree() { return Ar::kId == ArF32::kId ? 5 : kExpoTaylor; }
 
 // Vector slots of a group of T trajectories: psi_t and the batched product y_t
 // per trajectory, then the shared scratch (two product buffers and the Taylor
@@ -101,6 +109,7 @@ __device__ __forceinline__ void level_apply(const typename Ar::cplx *__restrict_
 template <class Ar, int G, int R, bool DENSE = false>
 struct Expo {
     using cplx = typename Ar::cplx;
+    static constexpr int K = expo_degree<Ar>();
     static constexpr int NP = G * R;
     const KernelArgs &a;
     const Group<G> &g;
@@ -215,7 +224,7 @@ struct Expo {
         cplx *dst = w0;
         const typename Ar::coef sc = Ar::coef_of(s);
 #pragma unroll 1
-        for (int m = kExpoTaylor; m >= 1; --m) {
+        for (int m = K; m >= 1; --m) {
             m_times(src, dst, Ar::cmul(sc, inv[m]), x);
             g.sync();
             ++n_rhs;
@@ -354,7 +363,7 @@ struct Expo {
         // u_m = M u_{m-1} / m, u_0 = base
         const cplx *prev = base;
 #pragma unroll 1
-        for (int m = 1; m <= kExpoTaylor; ++m) {
+        for (int m = 1; m <= K; ++m) {
             cplx *um = u(m);
             m_times(prev, um, inv[m], nullptr);
             g.sync();
@@ -365,11 +374,11 @@ struct Expo {
         // powers are formed once per evaluation in the arithmetic's coefficient
         // type (FP32 pairs or floats on the FP32 pipe, doubles for complex128)
         auto eval = [&](double s, double &fp) {
-            typename Ar::coef pw[kExpoTaylor + 1], dpw[kExpoTaylor + 1];
+            typename Ar::coef pw[K + 1], dpw[K + 1];
             const typename Ar::coef sc = Ar::coef_of(s);
             pw[0] = Ar::coef_of(1.0);
 #pragma unroll
-            for (int m = 1; m <= kExpoTaylor; ++m) {
+            for (int m = 1; m <= K; ++m) {
                 dpw[m] = Ar::cmul(Ar::cconst((double)m), pw[m - 1]);
                 pw[m] = Ar::cmul(pw[m - 1], sc);
             }
@@ -380,7 +389,7 @@ struct Expo {
                 if (row < a.n) {
                     typename Ar::acc y = Ar::zero(), yp = Ar::zero();
 #pragma unroll
-                    for (int m = 1; m <= kExpoTaylor; ++m) {
+                    for (int m = 1; m <= K; ++m) {
                         const cplx um = u(m)[row];
                         Ar::axpy(yp, dpw[m], um);
                         Ar::axpy(y, pw[m], um);
@@ -423,12 +432,12 @@ struct Expo {
         }
         // psi(s) into the product buffer that does not hold the base
         cplx *o = (base == A) ? B : A;
-        typename Ar::coef pw[kExpoTaylor + 1];
+        typename Ar::coef pw[K + 1];
         {
             const typename Ar::coef sc = Ar::coef_of(s);
             pw[0] = Ar::coef_of(1.0);
 #pragma unroll
-            for (int m = 1; m <= kExpoTaylor; ++m) pw[m] = Ar::cmul(pw[m - 1], sc);
+            for (int m = 1; m <= K; ++m) pw[m] = Ar::cmul(pw[m - 1], sc);
         }
 #pragma unroll 1
         for (int r2 = 0; r2 < R; ++r2) {
@@ -436,7 +445,7 @@ struct Expo {
             if (row < a.n) {
                 typename Ar::acc y = Ar::zero();
 #pragma unroll
-                for (int m = 1; m <= kExpoTaylor; ++m) Ar::axpy(y, pw[m], u(m)[row]);
+                for (int m = 1; m <= K; ++m) Ar::axpy(y, pw[m], u(m)[row]);
                 o[row] = Ar::add_scaled(base[row], Ar::coef_of(1.0), y);
             }
         }
