@@ -58,6 +58,7 @@ RUN_LAUNCHES = 3
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch at the bench's size
 # (one ncu pass, profiles/); an entry is removed when its kernel changes
 TRAFFIC_PER_LAUNCH = {
+    "qtm::mcwf_kernel<df64,32,2>": 14.04e6 + 236.46e6,   # 20,000 JC trajectories: outputs and spill evictions
     "qtm::dense_tc_kernel<256>": 54.81e9 + 55.78e9,      # 20,000 dense trajectories, seven products per attempt
 }
 
@@ -84,7 +85,8 @@ def parse():
                     help="skip the exponential-method legs (stiff Purcell system, Jaynes-Cummings)")
     ap.add_argument("--no-ising", action="store_true",
                     help="skip the batched Ising-chain measurement (L = 6..10 in one CUDA graph)")
-    ap.add_argument("--only", choices=["c128", "df64", "c64", "dense", "expo_purcell", "expo_jc", "expo_dense", "peak"],
+    ap.add_argument("--only", choices=["c128", "df64", "c64", "dense", "expo_purcell", "expo_jc", "expo_dense",
+                                       "expo_tc", "expo_prop", "peak"],
                     default=None,
                     help="time one arithmetic only (profiling); no observable-error comparison.  'dense': the "
                          "tensor-core engine on the dense N = 256 system with --ntraj trajectories")
@@ -485,6 +487,29 @@ def main():
                               "steps_per_trajectory": (st["accepted"] + st["rejected"]) / ntraj,
                               "gpu_launches": RUN_LAUNCHES * (args.steps + max(args.warmup, 0)), "clocks": clk,
                               "note": "tensor-core engine only (profiling run)"}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+    if args.only in ("expo_tc", "expo_prop"):
+        # one leg alone (profiling): the exponential method on the tensor cores on
+        # the dense workload, or the learned proposal in the exponential method's
+        # crossing search on the Jaynes-Cummings workload, --ntraj trajectories
+        if args.only == "expo_tc":
+            from paper_1810_03047_gb300 import systems as S
+            dprob = S.dense_random(ntraj=args.ntraj)
+            r = _timed_passes(Q, torch, stream, world, dist, dprob, Q.QTM_PREC_BF16X6, Q.QTM_METHOD_EXPONENTIAL,
+                              first, ntraj, passes=max(1, args.steps))
+            r.pop("mean")
+        else:
+            r = _learned_proposal_expo(Q, torch, stream, world, dist, prob, first, ntraj, ntraj)
+        clk = clocks.stop()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
+                              "steps": args.steps, "warmup": 1, "higher_is_better": True, "scaling": "weak",
+                              "vs_baseline": None, "data": "synthetic",
+                              "config": {"workload": args.only, "ntraj_per_gpu": ntraj}, "result": r,
+                              "gpu_launches": r.get("launches"), "clocks": clk,
+                              "note": "one leg only (profiling run)"}), flush=True)
         if world > 1:
             dist.destroy_process_group()
         return 0
