@@ -210,64 +210,79 @@ __device__ void role_mma(const DenseArgs &a, Pipe &p)
     tc::mma_commit(p.acc_full);
 }
 
-// The eight rows of one k-block a producer thread forms for product SS (0: the
-// rhs-mode input): the input wt_{SS-1} of the column (wt_0 = psi) read from device
-// memory, split into three bf16 terms and stored into the swizzled tiles (idle
-// columns: zero).
-template <int NP, int SS>
-__device__ __forceinline__ void produce_rows(const DenseArgs &a, long long tile_base, int pw, int lane, int kg,
-                                             const float *s_hf, const int *s_sel, unsigned char *ytile)
+// The eight rows of the tile a producer thread forms: their source rows in device
+// memory for product s (0: the rhs-mode input; else wt_{s-1} of the column, wt_0 =
+// psi), nullptr for an idle column or a row past the rhs-mode input (zero).
+template <int NP>
+__device__ __forceinline__ void producer_rows(const DenseArgs &a, int s, long long tile_base, int pw, int lane,
+                                              const float *s_hf, const int *s_sel, const float *(&src)[8])
 {
     constexpr int KD = 2 * NP;
-    const int chunk = ((lane & 15) * 4) >> 3, half8 = ((lane & 15) * 4) & 7;
     const size_t vs = (size_t)a.cols * KD;  // distance between the vectors of a column
-#pragma unroll 4
+    const int kk = (lane & 15) * 4;         // this thread's 4 values within a 64-wide k-block
+#pragma unroll
     for (int it = 0; it < 8; ++it) {
         const int row = 16 * pw + 2 * it + (lane >> 4);
-        float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
-        if constexpr (SS == 0) {
+        const float *p = nullptr;
+        if (a.mode == kDenseRhs) {
             const long long g = tile_base + row;
-            if (g < a.rhs_n) y = ld4(a.rhs_in + g * KD + kg);
-        } else {
-            if (s_hf[row] != 0.f) {
-                const int v = SS == 1 ? (s_sel[row] & 1) : kVK0 + SS - 2;  // psi, or wt_{SS-1}
-                y = ld4(a.state + (size_t)(tile_base + row) * KD + kg + v * vs);
-            }
+            if (g < a.rhs_n) p = a.rhs_in + g * KD + kk;
+        } else if (s_hf[row] != 0.f) {
+            const int v = s == 1 ? (s_sel[row] & 1) : kVK0 + s - 2;  // psi, or wt_{s-1}
+            p = a.state + (size_t)(tile_base + row) * KD + kk + v * vs;
         }
+        src[it] = p;
+    }
+}
+
+// This thread's eight values of k-block kb (four consecutive k each)
+__device__ __forceinline__ void producer_load(const float *const (&src)[8], int kb, float4 (&y)[8])
+{
+#pragma unroll
+    for (int it = 0; it < 8; ++it) y[it] = src[it] ? ld4(src[it] + kb * kKB) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+// ... split into three bf16 terms and stored into the swizzled tiles
+__device__ __forceinline__ void producer_store(const float4 (&y)[8], int pw, int lane, unsigned char *ytile)
+{
+    const int chunk = ((lane & 15) * 4) >> 3, half8 = ((lane & 15) * 4) & 7;
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+        const int row = 16 * pw + 2 * it + (lane >> 4);
         uint2 t[kSplits];
-        split4(y, t);
+        split4(y[it], t);
         const int off = row * 128 + ((chunk ^ (row & 7)) << 4) + half8 * 2;
 #pragma unroll
         for (int q = 0; q < kSplits; ++q) *reinterpret_cast<uint2 *>(ytile + q * kYTile + off) = t[q];
     }
 }
 
-// Producer warps: k-blocks of Y_s for the tile, then the epilogue K_s <- D.
+// Producer warps: k-blocks of the product's input for the tile, then the
+// epilogue.  The loads of k-block kb + 1 are issued before the wait for a free
+// tile and the split of k-block kb, so the device-memory latency overlaps the
+// ring's turnover instead of starving the tensor cores.
 template <int NP>
 __device__ void role_producer(const DenseArgs &a, Pipe &p, int s, long long tile_base, int pw, int lane,
                               const float *s_hf, const int *s_sel, const float *cf)
 {
     using S = TcShape<NP>;
     const bool rhs = a.mode == kDenseRhs;
-    const int kk = (lane & 15) * 4;  // this thread's 4 values within the 64-wide k-block
+    const float *src[8];
+    producer_rows<NP>(a, s, tile_base, pw, lane, s_hf, s_sel, src);
+    float4 nxt[8];
+    producer_load(src, 0, nxt);
     for (int kb = 0; kb < S::NKB; ++kb) {
+        float4 cur[8];
+#pragma unroll
+        for (int it = 0; it < 8; ++it) cur[it] = nxt[it];
+        if (kb + 1 < S::NKB) producer_load(src, kb + 1, nxt);
         const uint32_t ys = p.ycnt & 1, yph = (p.ycnt >> 1) & 1;
         if (!tc::mbar_wait(&p.y_empty[ys], yph ^ 1, p.abort, p.limit)) {
             raise_abort(a, p);
             return;
         }
         unsigned char *ytile = p.yt + ys * kSplits * kYTile;
-        const int kg = kb * kKB + kk;
-        switch (rhs ? 0 : s) {
-        case 0: produce_rows<NP, 0>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
-        case 1: produce_rows<NP, 1>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
-        case 2: produce_rows<NP, 2>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
-        case 3: produce_rows<NP, 3>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
-        case 4: produce_rows<NP, 4>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
-        case 5: produce_rows<NP, 5>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
-        case 6: produce_rows<NP, 6>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
-        default: produce_rows<NP, 7>(a, tile_base, pw, lane, kg, s_hf, s_sel, ytile); break;
-        }
+        producer_store(cur, pw, lane, ytile);
         tc::fence_proxy_async_smem();
         tc::mbar_arrive(&p.y_full[ys]);
         ++p.ycnt;
