@@ -55,6 +55,8 @@ struct ExpoSlots {
     static constexpr int kPsi = 0, kY = T, kA = 2 * T, kB = 2 * T + 1, kU = 2 * T + 2;
     static constexpr int kCount = kU + kExpoTaylor;
 };
+// apply_jump's dense path keeps every channel's product in u_1, u_2, ...
+static_assert(kJumpKeep <= kExpoTaylor, "the kept channel products fit the Taylor slots");
 
 // out_t = P x_t for t < T (x_t = x + t NP, out_t = out + t NP) on the lane's rows;
 // P is column-major with NP = G R rows per column (zero below n), so every

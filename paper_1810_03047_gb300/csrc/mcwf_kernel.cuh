@@ -131,7 +131,8 @@ __device__ __forceinline__ void spmv_rows(const CsrView<Ar> &A, const typename A
 
 // v[r] = (D x)[gl + G r] for a dense complex64 operator D, column-major with
 // column stride ld: one column per iteration, the group's rows of a column in
-// consecutive lanes (coalesced loads), x_c broadcast from shared memory
+// consecutive lanes (coalesced loads), x_c broadcast from shared memory; eight
+// columns in flight, as the ladder products (the operator streams from L2)
 template <int G, int R>
 __device__ __forceinline__ void dense_rows_f32(const float2 *D, int ld, const cpx<float> *x, int gl, int n,
                                                cpx<float> (&v)[R])
@@ -139,7 +140,7 @@ __device__ __forceinline__ void dense_rows_f32(const float2 *D, int ld, const cp
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = cpx<float>{0.f, 0.f};
     const float2 *col = D + gl;
-#pragma unroll 4
+#pragma unroll 8
     for (int c = 0; c < n; ++c) {
         const cpx<float> xc = x[c];
 #pragma unroll
@@ -465,21 +466,30 @@ __device__ __noinline__ double locate_crossing(const Coefs<Ar> &C, Lanes<Ar, G, 
 // vector (group synchronised).  Chooses the channel, writes C_n* y / ||C_n* y||
 // to psi (lane rows; tmp is lane-row scratch), and returns the channel (or -1
 // when every weight is zero).
+// Channels whose products apply_jump keeps (DENSE: the scratch vectors after tmp)
+constexpr int kJumpKeep = 9;
+
 template <class Ar, int G, int R, bool DENSE = false>
 __device__ __noinline__ int apply_jump(const KernelArgs &a, Group<G> g, const int *si,
                                        const typename Ar::real *sv, typename Ar::cplx *psi,
                                        typename Ar::cplx *tmp, const typename Ar::cplx *y, double ck)
 {
     const int gl = g.gl, n = a.n;
+    constexpr int NP = G * R;
+    // DENSE (the exponential method's lock-step kernel): tmp heads kJumpKeep
+    // scratch vectors, so each channel's C_q y is kept and the chosen one is not
+    // formed a second time
+    const bool keep = DENSE && a.n_c <= kJumpKeep;
     double wq[kMaxChannels];
     double wsum = 0.0;
     for (int q = 0; q < a.n_c; ++q) {
-        op_rows<Ar, G, R, DENSE>(a, 1 + q, si, sv, y, tmp, gl);
+        typename Ar::cplx *dst = keep ? tmp + q * NP : tmp;
+        op_rows<Ar, G, R, DENSE>(a, 1 + q, si, sv, y, dst, gl);
         typename Ar::red part = Ar::rzero();
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const int row = gl + G * r;
-            if (row < n) part = Ar::radd(part, Ar::abs2(tmp[row]));
+            if (row < n) part = Ar::radd(part, Ar::abs2(dst[row]));
         }
         wq[q] = Ar::rval(Ar::rsum(g, part));
         wsum += wq[q];
@@ -495,12 +505,13 @@ __device__ __noinline__ int apply_jump(const KernelArgs &a, Group<G> g, const in
             break;
         }
     }
-    op_rows<Ar, G, R, DENSE>(a, 1 + ch, si, sv, y, psi, gl);
+    if (!keep) op_rows<Ar, G, R, DENSE>(a, 1 + ch, si, sv, y, psi, gl);
+    const typename Ar::cplx *cy = keep ? tmp + ch * NP : psi;
     const double nc = sqrt(wq[ch]);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int row = gl + G * r;
-        if (row < n) psi[row] = Ar::div(psi[row], nc);
+        if (row < n) psi[row] = Ar::div(cy[row], nc);
     }
     return ch;
 }
