@@ -998,6 +998,126 @@ __device__ void lockstep_column(const KernelArgs &a, const Group<G> &g, const in
     }
 }
 
+// kLockInterval in a light instantiation of its own (the interval and start
+// launches): the same work as lockstep_column's interval mode, with one vector
+// slot per group and none of the crossing code, so that many more groups fit
+// per SM than in the catch-up's instantiation (13 slots, 128 registers).
+template <int G, int R>
+__device__ void lockstep_interval(const KernelArgs &a, const Group<G> &g, const int *si, const ArF32::real *sv,
+                                  ArF32::cplx *ybuf, long long il)
+{
+    using Ar = ArF32;
+    using cplx = Ar::cplx;
+    const int n = a.n, gl = g.gl, j = a.lock_j, half = a.lock_ld / 2;
+    LockCol *lc = static_cast<LockCol *>(a.lock_col) + il;
+    float *gpsi = a.lock_psi + (size_t)il * a.lock_ld;
+    auto norm2 = [&]() {
+        Ar::red nn = Ar::rzero();
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int row = gl + G * r;
+            if (row < n) nn = Ar::radd(nn, Ar::abs2(ybuf[row]));
+        }
+        return Ar::rval(Ar::rsum(g, nn));
+    };
+    ExpoTraj x;
+    int jdef = -1;
+    unsigned long long acc = 0, rhs = 0;
+    bool write_psi = false;
+    if (j == 0) {
+        // (A): psi0, the first draws, output 0
+        const cplx *psi0 = static_cast<const cplx *>(a.psi0);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int row = gl + G * r;
+            if (row < n) ybuf[row] = psi0[row];
+        }
+        g.sync();
+        x.k = 0;
+        jump_draws(a.seed, a.traj0 + il, 0, x.r, x.c);
+        x.t = a.t[0];
+        x.steps = 0;
+        x.status = 0;
+        x.jdone = a.n_t;
+        x.n_jump = 0;
+        record_outputs<Ar, G, R>(a, g, si, sv, ybuf, 0, a.out + (size_t)il * a.n_t * a.n_obs, nullptr);
+        x.nb = norm2();
+        write_psi = true;
+    } else {
+        x = lc->x;
+        jdef = lc->jdef;
+        if (x.status != 0 || jdef >= 0) return;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int row = gl + G * r;
+            if (row < n)  // y = psi + (P_L - I) psi
+                ybuf[row] = cplx{gpsi[row] + a.lock_y[(size_t)il * a.lock_ld + row],
+                                 gpsi[half + row] + a.lock_y[(size_t)il * a.lock_ld + half + row]};
+        }
+        g.sync();
+        rhs = 1;  // the tensor cores' product
+        const double nn = norm2();
+        if (nn < x.r) {  // a crossing: deferred to the catch-up
+            jdef = j;
+            if (gl == 0) a.lock_list[atomicAdd(&a.queue[0], 1ULL)] = (int)il;
+        } else {
+            ++x.steps;
+            if (!isfinite(nn)) {
+                x.status = 6;
+                x.jdone = j;
+            } else {
+                record_outputs<Ar, G, R>(a, g, si, sv, ybuf, j, a.out + (size_t)il * a.n_t * a.n_obs, nullptr);
+                x.nb = nn;
+                x.t = a.t[j];
+                acc = 1;
+                write_psi = true;
+            }
+        }
+    }
+    if (write_psi) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int row = gl + G * r;
+            if (row < n) {
+                gpsi[row] = ybuf[row].re;
+                gpsi[half + row] = ybuf[row].im;
+            }
+        }
+    }
+    const unsigned long long acc_tot = acc + (j == 0 ? 0 : lc->n_acc);
+    const unsigned long long rhs_tot = rhs + (j == 0 ? 0 : lc->n_rhs);
+    const unsigned long long rej_tot = j == 0 ? 0 : lc->n_rej;
+    const int root_tot = j == 0 ? 0 : lc->root_iters;
+    g.sync();  // every lane has read the record before lane 0 rewrites it
+    if (gl == 0) {
+        lc->x = x;
+        lc->jdef = jdef;
+        lc->n_acc = acc_tot;
+        lc->n_rhs = rhs_tot;
+        lc->n_rej = rej_tot;
+        lc->root_iters = root_tot;
+    }
+}
+
+template <int G, int R, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, (G <= 32 ? 6 : 3)) mcwf_expo_interval_kernel(const __grid_constant__ KernelArgs a)
+{
+    using Ar = ArF32;
+    using cplx = Ar::cplx;
+    constexpr int NP = G * R;
+    constexpr int GROUPS = BLOCK / G;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const Group<G> g(threadIdx.x, reinterpret_cast<unsigned long long *>(smem + a.smem_scratch_offset));
+    cplx *ybuf = reinterpret_cast<cplx *>(smem + a.smem_ybuf_offset) + (size_t)(threadIdx.x / G) * NP;
+    const int *si = a.ints;
+    const Ar::real *sv = static_cast<const Ar::real *>(a.vals);
+    for (long long il = (long long)blockIdx.x * GROUPS + threadIdx.x / G; il < a.ntraj;
+         il += (long long)gridDim.x * GROUPS) {
+        lockstep_interval<G, R>(a, g, si, sv, ybuf, il);
+        g.sync();
+    }
+}
+
 template <int G, int R, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, (G <= 32 ? 4 : 2)) mcwf_expo_lockstep_kernel(const __grid_constant__ KernelArgs a)
 {
@@ -1043,16 +1163,17 @@ cudaError_t launch_expo_lockstep_instance(const KernelArgs &a0, cudaStream_t str
     constexpr int GROUPS = BLOCK / G;
     KernelArgs a = a0;
     auto al16 = [](size_t x) { return (x + 15) & ~size_t(15); };
+    const bool light = a.lock_mode == kLockInterval;
     const size_t sb = al16((size_t)GROUPS * (Group<G>::kWarps + 1) * 8);
-    const size_t cb = al16((kExpoTaylor + 1) * sizeof(ArF32::coef));
+    const size_t cb = light ? 0 : al16((kExpoTaylor + 1) * sizeof(ArF32::coef));
     a.smem_vals_offset = 0;
     a.smem_scratch_offset = 0;
     a.smem_coef_offset = (int)sb;
     a.smem_mlp_offset = (int)(sb + cb);
     a.smem_ybuf_offset = (int)(sb + cb);
-    const size_t smem = sb + cb + (size_t)GROUPS * ExpoSlots<1>::kCount * G * R * sizeof(cplx);
+    const size_t smem = sb + cb + (size_t)GROUPS * (light ? 1 : ExpoSlots<1>::kCount) * G * R * sizeof(cplx);
     if (smem > 227 * 1024 || a.lock_ld < 2 * a.n) return cudaErrorInvalidValue;
-    auto kern = mcwf_expo_lockstep_kernel<G, R, BLOCK>;
+    auto kern = light ? mcwf_expo_interval_kernel<G, R, BLOCK> : mcwf_expo_lockstep_kernel<G, R, BLOCK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int dev = 0, sms = 0, nb = 0;
