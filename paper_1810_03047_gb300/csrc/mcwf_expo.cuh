@@ -34,6 +34,10 @@
 
 #include "mcwf_kernel.cuh"
 
+#ifndef QTM_EXP_LOCK_UNROLL
+#define QTM_EXP_LOCK_UNROLL 8
+#endif
+
 namespace qtm {
 
 constexpr int kExpoTaylor = 9;  // largest degree of the Taylor polynomial of exp(s M), s <= delta
@@ -62,7 +66,7 @@ static_assert(kJumpKeep <= kExpoTaylor, "the kept channel products fit the Taylo
 // P is column-major with NP = G R rows per column (zero below n), so every
 // column is loaded once for the T products.  nn[t] = the lane's part of
 // ||out_t||^2.  The x_t are synchronised.
-template <class Ar, int G, int R, int T>
+template <class Ar, int G, int R, int T, int U = 0>
 __device__ __forceinline__ void level_apply(const typename Ar::cplx *__restrict__ P, const typename Ar::cplx *x,
                                             typename Ar::cplx *out, int gl, int n, typename Ar::red (&nn)[T])
 {
@@ -77,7 +81,7 @@ __device__ __forceinline__ void level_apply(const typename Ar::cplx *__restrict_
     // registers (double-float, batches); eight for complex64 on multi-warp
     // groups, whose large P_L streams from L2 (dense N = 256: +6 %; on the
     // single-warp layouts eight measured 3-4 % slower)
-    constexpr int kUnroll = (T > 1 || Ar::kId == ArDF::kId) ? 2 : (Ar::kId == ArF32::kId && G >= 64 ? 8 : 4);
+    constexpr int kUnroll = U > 0 ? U : (T > 1 || Ar::kId == ArDF::kId) ? 2 : (Ar::kId == ArF32::kId && G >= 64 ? 8 : 4);
 #pragma unroll(kUnroll)
     for (int c = 0; c < n; ++c) {
         typename Ar::cplx p[R];
@@ -194,7 +198,7 @@ struct Expo {
     __device__ __forceinline__ typename Ar::red level_part_inl(int l, const cplx *x, cplx *out) const
     {
         typename Ar::red p[1];
-        level_apply<Ar, G, R, 1>(level(l), x, out, g.gl, a.n, p);
+        level_apply<Ar, G, R, 1, DENSE ? QTM_EXP_LOCK_UNROLL : 0>(level(l), x, out, g.gl, a.n, p);
         return p[0];
     }
     __device__ __noinline__ typename Ar::red level_part_ool(int l, const cplx *x, cplx *out) const

@@ -38,6 +38,13 @@
 //       of the accepted step.
 #pragma once
 
+#ifndef QTM_EXP_LOCK_UNROLL2
+#define QTM_EXP_LOCK_UNROLL2 8
+#endif
+namespace qtm {
+constexpr int kLockUnroll2 = QTM_EXP_LOCK_UNROLL2;
+}
+
 #include "proposal.cuh"
 #include "qtm_arith.cuh"
 #include "qtm_device.cuh"
@@ -140,7 +147,7 @@ __device__ __forceinline__ void dense_rows_f32(const float2 *D, int ld, const cp
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = cpx<float>{0.f, 0.f};
     const float2 *col = D + gl;
-#pragma unroll 8
+#pragma unroll (kLockUnroll2)
     for (int c = 0; c < n; ++c) {
         const cpx<float> xc = x[c];
 #pragma unroll
