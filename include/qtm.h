@@ -99,7 +99,9 @@ enum {
                            the six products of combined order <= 2 accumulated in
                            FP32 (as accurate as an FP32 product); state vectors FP32,
                            outputs, norms and root find as complex64 with FP64
-                           scalars.  No learned proposal, no layout choice */
+                           scalars.  No learned proposal, no layout choice.  With
+                           QTM_METHOD_EXPONENTIAL: the lock-step exponential
+                           method on the tensor cores (see qtm_set_method) */
 };
 
 /* Integrator of the no-jump evolution (qtm_set_method). */
@@ -473,7 +475,8 @@ qtm_status qtm_rhs_batch(qtm_ctx *ctx, int64_t n_vec, const double *y, double *m
  *     output spacing (uniform grids) or the largest output interval;
  *   - a trajectory moves from output to output with one dense product P_L psi
  *     (uniform grids) or with the binary digits of the interval in units of
- *     delta plus a degree-9 Taylor remainder;
+ *     delta plus a Taylor remainder (degree 9; degree 5 for the FP32 state of
+ *     QTM_PREC_C64 and QTM_PREC_BF16X6, whose truncation is then below 8.3e-11);
  *   - the squared norm cannot increase (d||psi||^2/dt = -sum_n ||C_n psi||^2),
  *     so a jump happened before t_j exactly when ||psi(t_j)||^2 < r (Algorithm 1
  *     (B)); the crossing is then bracketed within delta by a binary descent over
@@ -491,13 +494,26 @@ qtm_status qtm_rhs_batch(qtm_ctx *ctx, int64_t n_vec, const double *y, double *m
 /* Selects the method of later runs.  QTM_METHOD_EXPONENTIAL computes and uploads
  * the ladder (host FP64, O(L n^3 + 12 nnz(M) n) operations; (L + 1) n^2 complex
  * values of device memory, rounded to the context's arithmetic) and needs
- * QTM_PREC_C128, QTM_PREC_DF64 or QTM_PREC_C64 (FP32 propagators and state,
- * double-float norms: a trajectory's jump times move by about the FP32 rounding
- * accumulated over the products), dimension <= 256 and no time-dependent terms
- * (QTM_ERR_UNSUPPORTED otherwise).  The learned proposal works with it on the
- * contexts that support the proposal (complex128 or double-float, dimension <= 64;
- * see above).  QTM_METHOD_DOPRI5 restores the default.
- * QTM_ERR_ARG for any other value. */
+ * dimension <= 256 and no time-dependent terms (QTM_ERR_UNSUPPORTED otherwise),
+ * in any arithmetic:
+ *   QTM_PREC_C128, QTM_PREC_DF64, QTM_PREC_C64 (FP32 propagators and state,
+ *     double-float norms: a trajectory's jump times move by about the FP32
+ *     rounding accumulated over the products) -- one trajectory per lane group;
+ *   QTM_PREC_BF16X6 -- all trajectories of a run in lock step, which needs a
+ *     uniform output grid (QTM_ERR_UNSUPPORTED otherwise): per output interval
+ *     one tensor-core product forms (P_L - I) psi for every trajectory (the
+ *     engine's BF16x6 split, FP32 accumulation; the library adds psi in FP32),
+ *     and a per-interval kernel records the outputs; a trajectory whose norm
+ *     crosses its threshold inside the interval waits for a catch-up launch
+ *     (every eight intervals and after the last) that runs its crossing search,
+ *     jump and propagation in complex64 and the intervals it missed, after which
+ *     it rejoins.  Device memory per run: two FP32 state blocks of
+ *     ntraj x 2 x (dim rounded up to 64) values, 100 bytes per trajectory.
+ *     qtm_stats reports one product launch's device time (product_ms).
+ * The learned proposal works with it on the contexts that support the proposal
+ * (complex128 or double-float, dimension <= 64; see above).  QTM_METHOD_DOPRI5
+ * restores the default (for QTM_PREC_BF16X6 the Dormand-Prince tensor-core
+ * engine).  QTM_ERR_ARG for any other value. */
 qtm_status qtm_set_method(qtm_ctx *ctx, int32_t method);
 
 /* The exponential method's ladder (exp(M delta 2^l), the no-jump evolution of
