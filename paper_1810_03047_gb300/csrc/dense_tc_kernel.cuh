@@ -145,13 +145,15 @@ __device__ __forceinline__ void raise_abort(const DenseArgs &a, Pipe &p)
     atomicCAS(a.k.first_error, 0, kStatusTimeout);
 }
 
+// The roles of one product over the output chunks [c_lo, c_hi) (256 outputs
+// each; all of them except for the halves of a batched product's last wave)
 template <int NP>
-__device__ void role_tma(const DenseArgs &a, Pipe &p, const CUtensorMap *map)
+__device__ void role_tma(const DenseArgs &a, Pipe &p, const CUtensorMap *map, int c_lo, int c_hi)
 {
     using S = TcShape<NP>;
     for (int kb = 0; kb < S::NKB; ++kb)
         for (int split = 0; split < kSplits; ++split)
-            for (int c = 0; c < S::NCHUNK; ++c) {
+            for (int c = c_lo; c < c_hi; ++c) {
                 const uint32_t slot = p.ocnt % kOpRing, ph = (p.ocnt / kOpRing) & 1;
                 if (!tc::mbar_wait(&p.op_empty[slot], ph ^ 1, p.abort, p.limit)) {
                     raise_abort(a, p);
@@ -169,7 +171,7 @@ __device__ void role_tma(const DenseArgs &a, Pipe &p, const CUtensorMap *map)
 }
 
 template <int NP>
-__device__ void role_mma(const DenseArgs &a, Pipe &p)
+__device__ void role_mma(const DenseArgs &a, Pipe &p, int c_lo, int c_hi)
 {
     using S = TcShape<NP>;
     for (int kb = 0; kb < S::NKB; ++kb) {
@@ -181,7 +183,7 @@ __device__ void role_mma(const DenseArgs &a, Pipe &p)
         tc::tc_fence_after();
         const uint32_t ybase = tc::smem_u32(p.yt + ys * kSplits * kYTile);
         for (int split = 0; split < kSplits; ++split)
-            for (int c = 0; c < S::NCHUNK; ++c) {
+            for (int c = c_lo; c < c_hi; ++c) {
                 const uint32_t os = p.ocnt % kOpRing, oph = (p.ocnt / kOpRing) & 1;
                 if (!tc::mbar_wait(&p.op_full[os], oph, p.abort, p.limit)) {
                     raise_abort(a, p);
@@ -263,7 +265,7 @@ __device__ __forceinline__ void producer_store(const float4 (&y)[8], int pw, int
 // ring's turnover instead of starving the tensor cores.
 template <int NP>
 __device__ void role_producer(const DenseArgs &a, Pipe &p, int s, long long tile_base, int pw, int lane,
-                              const float *s_hf, const int *s_sel, const float *cf)
+                              const float *s_hf, const int *s_sel, const float *cf, int c_lo, int c_hi)
 {
     using S = TcShape<NP>;
     const bool rhs = a.mode == kDenseRhs;
@@ -308,10 +310,12 @@ __device__ void role_producer(const DenseArgs &a, Pipe &p, int s, long long tile
         dst = c.vec(wvec(s));  // wt_s
     }
     const uint32_t tbase = p.tmem + ((uint32_t)(32 * quarter) << 16);
+    // a chunk-split product (NP = 256: chunk c = the outputs of epilogue half c)
+    const bool skip = c_hi - c_lo < S::NCHUNK && (hsel < c_lo || hsel >= c_hi);
     // 64 columns per round: four loads in flight, one wait
     static_assert(S::HALF % 64 == 0, "epilogue rounds of 64 columns");
 #pragma unroll 1
-    for (int cc = hsel * S::HALF; cc < (hsel + 1) * S::HALF; cc += 64) {
+    for (int cc = hsel * S::HALF; cc < (skip ? hsel * S::HALF : (hsel + 1) * S::HALF); cc += 64) {
         uint32_t v[4][16];
 #pragma unroll
         for (int b = 0; b < 4; ++b) tc::tmem_ld16_async(tbase + cc + 16 * b, v[b]);
@@ -331,19 +335,20 @@ __device__ void role_producer(const DenseArgs &a, Pipe &p, int s, long long tile
 
 template <int NP>
 __device__ void stage_product(const DenseArgs &a, Pipe &p, const CUtensorMap *map, int s, long long tile_base,
-                              const float *s_hf, const int *s_sel, const float *cf)
+                              const float *s_hf, const int *s_sel, const float *cf, int c_lo = 0,
+                              int c_hi = TcShape<NP>::NCHUNK)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (warp == 0) {
-        if (lane == 0) role_tma<NP>(a, p, map);
+        if (lane == 0) role_tma<NP>(a, p, map, c_lo, c_hi);
         // keep the lanes' copies of the ring position in step with lane 0
         p.ocnt = __shfl_sync(0xffffffffu, p.ocnt, 0);
     } else if (warp == 1) {
-        if (lane == 0) role_mma<NP>(a, p);
+        if (lane == 0) role_mma<NP>(a, p, c_lo, c_hi);
         p.ocnt = __shfl_sync(0xffffffffu, p.ocnt, 0);
         p.ycnt = __shfl_sync(0xffffffffu, p.ycnt, 0);
     } else {
-        role_producer<NP>(a, p, s, tile_base, warp - 2, lane, s_hf, s_sel, cf);
+        role_producer<NP>(a, p, s, tile_base, warp - 2, lane, s_hf, s_sel, cf, c_lo, c_hi);
         // K_s is complete in device memory before any producer reads it
         asm volatile("bar.sync 1, %0;" ::"n"(kProducers) : "memory");
     }
@@ -1032,9 +1037,22 @@ __global__ void __launch_bounds__(kThreadsTc, 1)
     p.limit = a.wait_limit_ns ? a.wait_limit_ns : tc::kWaitLimitNs;
 
     if (a.mode == kDenseRhs) {
-        const long long tiles = (a.rhs_n + kTcCols - 1) / kTcCols;
-        for (long long tile = blockIdx.x; tile < tiles && !*s_abort; tile += gridDim.x)
-            stage_product<NP>(a, p, &opmap, 0, tile * kTcCols, s_hf, s_sel, cf);
+        // Tiles of 128 vectors; the r = tiles mod CTAs tiles of a partial last
+        // wave are split into their two output chunks (NP = 256, where a chunk
+        // is one epilogue half), so that wave takes half a tile's time: 157 tiles
+        // on 152 CTAs end after 1.5 tile-times instead of 2.
+        const long long tiles = (a.rhs_n + kTcCols - 1) / kTcCols, ctas = gridDim.x;
+        const long long r = (S::NCHUNK == 2 && S::HALF == 256 && tiles > ctas) ? tiles % ctas : 0;
+        const long long full = tiles - r, items = full + 2 * r;
+        for (long long i = blockIdx.x; i < items && !*s_abort; i += ctas) {
+            if (i < full) {
+                stage_product<NP>(a, p, &opmap, 0, i * kTcCols, s_hf, s_sel, cf);
+            } else {
+                const long long h = i - full;
+                const int c = (int)(h & 1);
+                stage_product<NP>(a, p, &opmap, 0, (full + h / 2) * kTcCols, s_hf, s_sel, cf, c, c + 1);
+            }
+        }
     } else {
         const long long tile_base = (long long)blockIdx.x * kTcCols;
         if (warp >= 2) {

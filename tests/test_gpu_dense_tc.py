@@ -63,6 +63,29 @@ def test_product_matches_fp64(orc, name, kw, n_vec, capsys):
     assert np.all(err <= scale * 2.0 ** -18)
 
 
+def test_product_with_a_split_last_wave(orc):
+    """More 128-vector tiles than CTAs (20,000 vectors: 157 tiles on 152 SMs):
+    the tiles of the partial last wave are split into their two 256-output
+    chunks, each CTA writing one half; every vector's product meets the bars of
+    test_product_matches_fp64."""
+    prob = S.dense_random(N=256)
+    ctx = Q.qtm_create(prob, precision=TC)
+    rng = np.random.default_rng(17)
+    n_vec = 20000
+    y = rng.standard_normal((n_vec, prob.dim)) + 1j * rng.standard_normal((n_vec, prob.dim))
+    y = y.astype(np.complex64).astype(np.complex128)
+    got = Q.qtm_rhs_batch(ctx, y)
+    Q.qtm_destroy(ctx)
+    M = orc.effective_matrix(prob)
+    ref = y @ M.T
+    err = np.abs(got - ref)
+    scale = np.abs(y) @ np.abs(M).T
+    assert np.all(err <= scale * 2.0 ** -18)
+    # the vectors of the split tiles (the last 5 x 128 up to 20,000) as accurate as the rest
+    tail = slice(152 * 128, n_vec)
+    assert float((err[tail] / scale[tail]).max()) <= 2.0 ** -18
+
+
 def test_rhs_batch_needs_the_tensor_core_precision():
     prob = S.jaynes_cummings_driven()
     ctx = Q.qtm_create(prob, precision=Q.QTM_PREC_C128)
