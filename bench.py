@@ -335,7 +335,7 @@ def _bf16x6_peak(sustained=True):
     return (1700.0 if sustained else 1900.0) / 6.0, "fallback bf16 peak / 6, of fallback"
 
 
-def lockstep_launches(n_t, every=8):
+def lockstep_launches(n_t, every=16):
     """Kernels of one lock-step exponential run on the tensor cores: a tensor-core
     product per output interval, the per-interval kernel per output, a catch-up
     every `every` intervals and after the last, the finish, and the reduction."""

@@ -505,7 +505,7 @@ qtm_status qtm_rhs_batch(qtm_ctx *ctx, int64_t n_vec, const double *y, double *m
  *     engine's BF16x6 split, FP32 accumulation; the library adds psi in FP32),
  *     and a per-interval kernel records the outputs; a trajectory whose norm
  *     crosses its threshold inside the interval waits for a catch-up launch
- *     (every eight intervals and after the last) that runs its crossing search,
+ *     (every sixteen intervals and after the last) that runs its crossing search,
  *     jump and propagation in complex64 and the intervals it missed, after which
  *     it rejoins.  Device memory per run: two FP32 state blocks of
  *     ntraj x 2 x (dim rounded up to 64) values, 100 bytes per trajectory.

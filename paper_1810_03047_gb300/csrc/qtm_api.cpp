@@ -1008,8 +1008,11 @@ static qtm_status enqueue_run(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64
             // the lock step until the next catch-up launch (every kCatchUpEvery
             // intervals and after the last), which resolves the deferred columns
             // with every group of the GPU working through the list, instead of
-            // each interval waiting for its slowest crossing
-            constexpr int kCatchUpEvery = 8;
+            // each interval waiting for its slowest crossing.  Measured on the
+            // dense N = 256 workload: every 4 intervals 416k trajectories/s, 8
+            // 475k, 12 493k, 16 507k (fewer, fuller catch-ups outweigh the extra
+            // intervals a deferred column then makes up on the ladder)
+            constexpr int kCatchUpEvery = 16;
             ctx->product_timed = with_events && ctx->n_t > 1;
             auto lockstep = [&](int mode, int j) -> qtm_status {
                 a.lock_mode = mode;
