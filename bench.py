@@ -875,7 +875,10 @@ def exponential_method(Q, torch, stream, world, rank, dist, pk, jc_ref_mean, ntr
     Dormand-Prince path.  Roofline of the exponential kernel on the
     Jaynes-Cummings workload: per trajectory and output interval one dense
     product P x (N^2 complex multiply-adds = 8 N^2 flops), against the FP64 peak
-    (complex128) or the double-float emulation peak."""
+    (complex128) or the double-float emulation peak.  On the dense workload also
+    the lock-step form on the tensor cores (QTM_PREC_BF16X6): its product launch
+    ((P_L - I) psi for all trajectories, 8 N^2 flops each) against the bf16 peak
+    over six."""
     from paper_1810_03047_gb300 import shards
     from paper_1810_03047_gb300 import systems as S
     first, count = shards.shard(world * ntraj, world, rank)

@@ -1010,8 +1010,9 @@ static qtm_status enqueue_run(qtm_ctx *ctx, int64_t first, int64_t ntraj, uint64
             // with every group of the GPU working through the list, instead of
             // each interval waiting for its slowest crossing.  Measured on the
             // dense N = 256 workload: every 4 intervals 416k trajectories/s, 8
-            // 475k, 12 493k, 16 507k (fewer, fuller catch-ups outweigh the extra
-            // intervals a deferred column then makes up on the ladder)
+            // 475k, 12 493k, 16 507k, 24 and 32 the same as 16 (fewer, fuller
+            // catch-ups outweigh the extra intervals a deferred column then makes
+            // up on the ladder, up to 16)
             constexpr int kCatchUpEvery = 16;
             ctx->product_timed = with_events && ctx->n_t > 1;
             auto lockstep = [&](int mode, int j) -> qtm_status {
