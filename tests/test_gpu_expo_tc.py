@@ -8,7 +8,7 @@ trajectories of a run together: per interval one tcgen05 product forms
 accumulation), y = psi + that is added in FP32, and a per-interval kernel
 finishes each column in complex64 arithmetic -- the outputs, or, for a column
 whose norm crosses its threshold, the crossing search on the ladder, the jump
-and the propagation on to the output time (in a catch-up launch every few
+and the propagation on to the output time (in a catch-up launch every sixteen
 intervals, after which the column rejoins the lock step).
 
 Bars: the complex64 ones against the exact oracle (expm between jumps, brentq
@@ -84,6 +84,21 @@ def test_same_trajectories_as_the_simt_complex64_path():
     assert np.mean(a["n_jumps"] == b["n_jumps"]) >= 0.98
     assert np.abs(a["mean"] - b["mean"]).max() <= 5e-4
     assert b["stats"]["failed"] == 0 and b["stats"]["jumps"] > 1000
+
+
+def test_full_size_run_against_the_simt_complex64_path():
+    """The dense workload at the bench's size (20,000 trajectories: 157 product
+    tiles, so the last wave is split by output chunk, and about 18,000 deferred
+    crossings over seven catch-up launches) against the per-trajectory complex64
+    kernel on the same ids: the same jumps for the bulk, the ensembles within a
+    few 1e-4, no failed trajectory, every output finite."""
+    prob = S.dense_random(ntraj=20000)
+    a = expo_run(prob, 20000, precision=Q.QTM_PREC_C64, record=4)
+    b = expo_run(prob, 20000, precision=TC, record=4)
+    assert np.mean(a["n_jumps"] == b["n_jumps"]) >= 0.98
+    assert np.abs(a["mean"] - b["mean"]).max() <= 5e-4
+    assert b["stats"]["failed"] == 0 and b["stats"]["jumps"] > 15000
+    assert np.all(np.isfinite(b["obs"]))
 
 
 @pytest.mark.parametrize("ntraj", [1, 127, 130, 300])
