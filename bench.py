@@ -59,7 +59,7 @@ RUN_LAUNCHES = 3
 # (one ncu pass, profiles/); an entry is removed when its kernel changes
 TRAFFIC_PER_LAUNCH = {
     "qtm::mcwf_kernel<df64,32,2>": 14.04e6 + 236.46e6,   # 20,000 JC trajectories: outputs and spill evictions
-    "qtm::dense_tc_kernel<256>": 54.81e9 + 55.78e9,      # 20,000 dense trajectories, seven products per attempt
+    "qtm::dense_tc_kernel<256>": 55.05e9 + 55.78e9,      # 20,000 dense trajectories, seven products per attempt
 }
 
 
