@@ -48,3 +48,22 @@ def test_gpu_arm_profiling_line():
     assert rl["traffic"] is None  # traffic is reported for the full-size launch only
     assert d["gpu_launches"] > 0 and d["value"] > 0
     assert "sm_mhz" in d["clocks"] and "reasons" in d["clocks"]
+
+
+def test_lockstep_launch_count_follows_the_library_schedule():
+    """The bench's `gpu_launches` for the lock-step exponential path counts the
+    library's schedule: its default catch-up cadence is the one the library's
+    run enqueues, and at a catch-up every eight intervals the count per run is
+    217 (the ncu launch list of two runs of that build held 434 launches)."""
+    import importlib.util
+    import inspect
+    import re
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    with open(os.path.join(ROOT, "paper_1810_03047_gb300", "csrc", "qtm_api.cpp")) as f:
+        every = int(re.search(r"kCatchUpEvery\s*=\s*(\d+)", f.read()).group(1))
+    assert inspect.signature(bench.lockstep_launches).parameters["every"].default == every
+    assert bench.lockstep_launches(101, every=8) == 217
+    # 100 products, 101 per-interval launches, 7 catch-ups, the finish, the reduction
+    assert bench.lockstep_launches(101, every=16) == 100 + 101 + 7 + 1 + 2
